@@ -1,0 +1,173 @@
+"""Plain FP64 CPU oracle for the eigenstate-basis TDSE propagator.
+
+TEST INFRASTRUCTURE ONLY.  The test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only users of this package; the GPU
+library never imports, links or calls it, and it shares no code with the GPU
+library.  The arithmetic lives in ``tdse_oracle.c`` (plain loops, FP64); this
+module only compiles it with gcc and marshals numpy arrays through ctypes.
+
+Functions follow the paper (Ó Broin & Nikolopoulos, arXiv:1201.6062):
+  dmatvec / hmatvec   Sec. 4, block form of the Hamiltonian-vector product
+  rk4                 App. B, Eqs. "RKFinal"/"RKDeriv", classic tableau
+  taylor              App. B, Eq. "taylor" (recursion read as T_m = dt/m M T_{m-1})
+  populations         Sec. 5 (continuum population = ionisation), Sec. 5.1 (unitarity)
+  adjoint             discrete adjoint of rk4 / taylor (the paper has no adjoint;
+                      pinned by finite differences and a forward-mode tangent)
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tdse_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force=False):
+    """Compile tdse_oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        L, I, D = ctypes.c_long, ctypes.c_int, ctypes.c_double
+        lib.orc_threads.restype = I
+        lib.orc_set_threads.argtypes = [I]
+        lib.orc_dmatvec.argtypes = [I, I, _dp, _dp, _dp]
+        lib.orc_hmatvec.argtypes = [I, I, _dp, _dp, D, _dp, _dp]
+        lib.orc_field_at.argtypes = [_dp, I, L, I]
+        lib.orc_field_at.restype = D
+        lib.orc_rk4.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L]
+        lib.orc_rk4.restype = L
+        lib.orc_taylor.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I]
+        lib.orc_taylor.restype = L
+        lib.orc_populations.argtypes = [I, I, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.orc_adjoint.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I, I, _dp, _dp, _dp]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _cvec(c):
+    """complex128 vector -> contiguous interleaved float64 view (copy)."""
+    c = np.ascontiguousarray(c, dtype=np.complex128).copy()
+    return c, c.view(np.float64)
+
+
+def _dims(E, U, lmax, n):
+    E = _f64(E).reshape(-1)
+    if lmax > 0:
+        U = _f64(U).reshape(lmax, n, n)
+    else:
+        U = np.zeros((1,), np.float64)
+    assert E.size == (lmax + 1) * n
+    return E, U
+
+
+def threads():
+    return _load().orc_threads()
+
+
+def set_threads(t):
+    _load().orc_set_threads(int(t))
+
+
+def dmatvec(lmax, n, U, x):
+    """y = D x (dipole part only)."""
+    _, U = _dims(np.zeros((lmax + 1) * n), U, lmax, n)
+    x, xv = _cvec(x)
+    y = np.zeros_like(x)
+    _load().orc_dmatvec(lmax, n, _p(U), _p(xv), _p(y.view(np.float64)))
+    return y
+
+
+def hmatvec(lmax, n, E, U, f, x):
+    """y = H(f) x = E o x + f D x."""
+    E, U = _dims(E, U, lmax, n)
+    x, xv = _cvec(x)
+    y = np.zeros_like(x)
+    _load().orc_hmatvec(lmax, n, _p(E), _p(U), float(f), _p(xv), _p(y.view(np.float64)))
+    return y
+
+
+def field_at(F, samples_per_step, k, h):
+    F = _f64(F)
+    return _load().orc_field_at(_p(F), samples_per_step, k, h)
+
+
+def _check_field(F, sps, nsteps):
+    F = _f64(F).reshape(-1)
+    need = (2 * nsteps + 1) if sps == 2 else (nsteps + 1)
+    if sps not in (1, 2) or F.size < need:
+        raise ValueError("field needs %d samples for samples_per_step=%d" % (need, sps))
+    return F
+
+
+def rk4(lmax, n, E, U, c0, F, dt, nsteps, samples_per_step=1):
+    """Propagate c0 over nsteps classic RK4 steps; returns (c, matvec_count)."""
+    E, U = _dims(E, U, lmax, n)
+    F = _check_field(F, samples_per_step, nsteps)
+    c, cv = _cvec(c0)
+    nmv = _load().orc_rk4(lmax, n, _p(E), _p(U), _p(cv), _p(F), samples_per_step, float(dt), int(nsteps))
+    return c, nmv
+
+
+def taylor(lmax, n, E, U, c0, F, dt, nsteps, order, samples_per_step=1, hold=0):
+    """Propagate c0 over nsteps truncated-Taylor steps of the given order."""
+    E, U = _dims(E, U, lmax, n)
+    F = _check_field(F, samples_per_step, nsteps)
+    c, cv = _cvec(c0)
+    nmv = _load().orc_taylor(lmax, n, _p(E), _p(U), _p(cv), _p(F), samples_per_step, float(dt),
+                             int(nsteps), int(order), int(hold))
+    return c, nmv
+
+
+def populations(lmax, n, E, c):
+    """Returns dict(per_state, per_l, bound, ionised, norm)."""
+    E = _f64(E).reshape(-1)
+    c, cv = _cvec(c)
+    N = (lmax + 1) * n
+    ps = np.zeros(N)
+    pl = np.zeros(lmax + 1)
+    b = ctypes.c_double()
+    io = ctypes.c_double()
+    nr = ctypes.c_double()
+    _load().orc_populations(lmax, n, _p(E), _p(cv), _p(ps), _p(pl), ctypes.byref(b), ctypes.byref(io),
+                            ctypes.byref(nr))
+    return dict(per_state=ps, per_l=pl, bound=b.value, ionised=io.value, norm=nr.value)
+
+
+def adjoint(lmax, n, E, U, c0, F, dt, nsteps, weights, scheme="rk4", order=4, samples_per_step=1, hold=0):
+    """Loss L = sum w |c(T)|^2 and its gradient with respect to every field sample.
+
+    Returns (grad[F.shape], c_final, loss)."""
+    E, U = _dims(E, U, lmax, n)
+    F = _check_field(F, samples_per_step, nsteps)
+    w = _f64(weights).reshape(-1)
+    assert w.size == (lmax + 1) * n
+    c, cv = _cvec(c0)
+    grad = np.zeros_like(F)
+    loss = ctypes.c_double()
+    sch = 0 if scheme == "rk4" else 1
+    _load().orc_adjoint(lmax, n, _p(E), _p(U), _p(cv), _p(F), samples_per_step, float(dt), int(nsteps),
+                        sch, int(order), int(hold), _p(w), _p(grad), ctypes.byref(loss))
+    return grad, c, loss.value

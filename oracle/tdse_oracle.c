@@ -1,0 +1,384 @@
+/*
+ * Plain FP64 CPU oracle for the laser-driven hydrogen TDSE propagated in the
+ * field-free eigenstate basis (Ó Broin & Nikolopoulos, "An OpenCL
+ * implementation for the solution of TDSE on GPU and CPU architectures").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * statement of what the GPU library computes.  Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or helper with the CUDA library and never includes it.
+ *
+ * Notation (paper Sec. 3.1 and Sec. 4):
+ *   blocks l = 0..lmax, n states per block, N = (lmax+1)*n amplitudes,
+ *   block l occupies amplitudes [l*n, (l+1)*n).
+ *   E[N]            field-free energies (the diagonal blocks E_L^d).
+ *   U[lmax][n][n]   row-major upper dipole blocks U_l = D_{l,l+1}; the lower
+ *                   block D_{l+1,l} is U_l^T and is not stored (Sec. 5,
+ *                   storage of the Hamiltonian array).
+ *   H(f) = diag(E) + f*D,  D block-tridiagonal, real symmetric (Sec. 3.1,
+ *   Fig. "Matrix"; length gauge, Sec. 5).
+ *   The ODE is dC/dt = M(t) C with M = -i H(t)  (Sec. 4, Eq. "ode").
+ * Complex vectors are interleaved (re, im) doubles.
+ *
+ * Field samples (reading of the paper, which is silent here):
+ *   samples_per_step = 1: F[k] = f(t0 + k*dt), k = 0..nsteps; the value at
+ *       a half step is the mean of its two neighbours.
+ *   samples_per_step = 2: F[h] = f(t0 + h*dt/2), h = 0..2*nsteps.
+ *
+ * Parity pins (tests/test_oracle_pins.py): brute-force dense H on tiny
+ * sizes, the closed-form field-free evolution of each scheme, the two-level
+ * Rabi flop, scipy expm / solve_ivp references, RK4 == Taylor-4 for constant
+ * H, convergence orders, central finite differences and a forward-mode
+ * tangent for the adjoint.
+ */
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/*
+ * y = D x, the dipole part of the Hamiltonian-vector product (Sec. 4, the
+ * block form of H C): block l of the result is
+ *     U_l x_{l+1}  (l < lmax)   +   U_{l-1}^T x_{l-1}  (l > 0).
+ * One sweep over each stored block gives both products: the row dot
+ * products feed block l and the row-scaled accumulation feeds block l+1.
+ */
+void orc_dmatvec(int lmax, int n, const double *U, const double *x, double *y)
+{
+    const long nn = (long)n * n;
+    const long N = (long)(lmax + 1) * n;
+    for (long a = 0; a < 2 * N; ++a) y[a] = 0.0;
+    if (lmax < 1 || n < 1) return;
+    double *up = (double *)calloc((size_t)(2 * N), sizeof(double)); /* U_l x_{l+1} into block l   */
+    double *dn = (double *)calloc((size_t)(2 * N), sizeof(double)); /* U_l^T x_l into block l+1  */
+#pragma omp parallel for schedule(static)
+    for (int l = 0; l < lmax; ++l) {
+        const double *Ul = U + (long)l * nn;
+        const double *xl = x + 2L * l * n;        /* block l   */
+        const double *xu = x + 2L * (l + 1) * n;  /* block l+1 */
+        double *rowsum = up + 2L * l * n;
+        double *colsum = dn + 2L * (l + 1) * n;
+        for (int i = 0; i < n; ++i) {
+            const double *row = Ul + (long)i * n;
+            double re = 0.0, im = 0.0;
+            for (int j = 0; j < n; ++j) {
+                re += row[j] * xu[2 * j];
+                im += row[j] * xu[2 * j + 1];
+            }
+            rowsum[2 * i] = re;
+            rowsum[2 * i + 1] = im;
+            const double xr = xl[2 * i], xi = xl[2 * i + 1];
+            for (int j = 0; j < n; ++j) {
+                colsum[2 * j] += row[j] * xr;
+                colsum[2 * j + 1] += row[j] * xi;
+            }
+        }
+    }
+    for (long a = 0; a < 2 * N; ++a) y[a] = up[a] + dn[a];
+    free(up);
+    free(dn);
+}
+
+/* y = H(f) x = E o x + f D x   (Sec. 4, Eq. "tdse_ode_c" with V = f D). */
+void orc_hmatvec(int lmax, int n, const double *E, const double *U, double f,
+                 const double *x, double *y)
+{
+    const long N = (long)(lmax + 1) * n;
+    orc_dmatvec(lmax, n, U, x, y);
+    for (long a = 0; a < N; ++a) {
+        y[2 * a] = E[a] * x[2 * a] + f * y[2 * a];
+        y[2 * a + 1] = E[a] * x[2 * a + 1] + f * y[2 * a + 1];
+    }
+}
+
+/* k = M x = -i H(f) x, the derivative of Sec. 4 (Eq. "ode"). */
+static void deriv(int lmax, int n, const double *E, const double *U, double f,
+                  const double *x, double *k)
+{
+    const long N = (long)(lmax + 1) * n;
+    orc_hmatvec(lmax, n, E, U, f, x, k);
+    for (long a = 0; a < N; ++a) {       /* -i (p + i q) = q - i p */
+        const double p = k[2 * a], q = k[2 * a + 1];
+        k[2 * a] = q;
+        k[2 * a + 1] = -p;
+    }
+}
+
+/* Field value at t_k + h*dt/2, h in {0, 1, 2} (reading stated in the header). */
+double orc_field_at(const double *F, int samples_per_step, long k, int h)
+{
+    if (samples_per_step == 2) return F[2 * k + h];
+    if (h == 0) return F[k];
+    if (h == 2) return F[k + 1];
+    return 0.5 * (F[k] + F[k + 1]);
+}
+
+/* v = a + s*b on complex vectors of N amplitudes (s real). */
+static void axpy_to(long N, const double *a, double s, const double *b, double *v)
+{
+    for (long q = 0; q < 2 * N; ++q) v[q] = a[q] + s * b[q];
+}
+
+/*
+ * One classic RK4 step, App. B Eqs. "RKFinal"/"RKDeriv" with the classic
+ * tableau c = (0, 1/2, 1/2, 1), a21 = a32 = 1/2, a43 = 1, b = (1,2,2,1)/6.
+ * If stages != NULL the stage inputs x1 = c, x2, x3, x4 are stored there
+ * (4*2N doubles) for the adjoint.
+ */
+static void rk4_step(int lmax, int n, const double *E, const double *U,
+                     double *c, double f0, double fh, double f1, double dt,
+                     double *work, double *stages)
+{
+    const long N = (long)(lmax + 1) * n;
+    double *k1 = work, *k2 = work + 2 * N, *k3 = work + 4 * N, *k4 = work + 6 * N;
+    double *x = work + 8 * N;
+    deriv(lmax, n, E, U, f0, c, k1);
+    axpy_to(N, c, 0.5 * dt, k1, x);
+    if (stages) { memcpy(stages, c, sizeof(double) * 2 * N); memcpy(stages + 2 * N, x, sizeof(double) * 2 * N); }
+    deriv(lmax, n, E, U, fh, x, k2);
+    axpy_to(N, c, 0.5 * dt, k2, x);
+    if (stages) memcpy(stages + 4 * N, x, sizeof(double) * 2 * N);
+    deriv(lmax, n, E, U, fh, x, k3);
+    axpy_to(N, c, dt, k3, x);
+    if (stages) memcpy(stages + 6 * N, x, sizeof(double) * 2 * N);
+    deriv(lmax, n, E, U, f1, x, k4);
+    for (long q = 0; q < 2 * N; ++q)
+        c[q] = c[q] + dt / 6.0 * (k1[q] + 2.0 * k2[q] + 2.0 * k3[q] + k4[q]);
+}
+
+/* Propagate c (in/out) over nsteps RK4 steps; returns the number of
+ * Hamiltonian-vector products performed (4 per step). */
+long orc_rk4(int lmax, int n, const double *E, const double *U, double *c,
+             const double *F, int samples_per_step, double dt, long nsteps)
+{
+    const long N = (long)(lmax + 1) * n;
+    double *work = (double *)malloc(sizeof(double) * 10 * N);
+    for (long k = 0; k < nsteps; ++k)
+        rk4_step(lmax, n, E, U, c, orc_field_at(F, samples_per_step, k, 0),
+                 orc_field_at(F, samples_per_step, k, 1),
+                 orc_field_at(F, samples_per_step, k, 2), dt, work, NULL);
+    free(work);
+    return 4 * nsteps;
+}
+
+/*
+ * Truncated Taylor step of order K (App. B, Eq. "taylor"), with the
+ * derivative recursion read as T_0 = c, T_m = (dt/m) M T_{m-1}, so that
+ * c(t+dt) = sum_{m=0..K} T_m = sum_m (-i H dt)^m / m! c.  H is frozen over
+ * the step at the field value fhold.  If terms != NULL, T_0..T_{K-1} are
+ * stored there for the adjoint.
+ */
+static void taylor_step(int lmax, int n, const double *E, const double *U,
+                        double *c, double fhold, double dt, int K, double *work,
+                        double *terms)
+{
+    const long N = (long)(lmax + 1) * n;
+    double *T = work, *Tn = work + 2 * N, *S = work + 4 * N;
+    memcpy(T, c, sizeof(double) * 2 * N);
+    memcpy(S, c, sizeof(double) * 2 * N);
+    for (int m = 1; m <= K; ++m) {
+        if (terms) memcpy(terms + (long)(m - 1) * 2 * N, T, sizeof(double) * 2 * N);
+        deriv(lmax, n, E, U, fhold, T, Tn);
+        for (long q = 0; q < 2 * N; ++q) {
+            T[q] = (dt / m) * Tn[q];
+            S[q] += T[q];
+        }
+    }
+    memcpy(c, S, sizeof(double) * 2 * N);
+}
+
+/* hold = 0: H frozen at t_k (the paper's "known time t"); hold = 1: at t_k + dt/2. */
+static double taylor_field(const double *F, int sps, long k, int hold)
+{
+    return orc_field_at(F, sps, k, hold ? 1 : 0);
+}
+
+long orc_taylor(int lmax, int n, const double *E, const double *U, double *c,
+                const double *F, int samples_per_step, double dt, long nsteps,
+                int K, int hold)
+{
+    const long N = (long)(lmax + 1) * n;
+    double *work = (double *)malloc(sizeof(double) * 6 * N);
+    for (long k = 0; k < nsteps; ++k)
+        taylor_step(lmax, n, E, U, c, taylor_field(F, samples_per_step, k, hold), dt, K, work, NULL);
+    free(work);
+    return (long)K * nsteps;
+}
+
+/*
+ * Norm and populations (Sec. 5: the continuum population after the pulse is
+ * the ionisation; Sec. 5.1: unitarity as an error measure).  bound sums
+ * |c_j|^2 over E_j < 0, ionised over E_j >= 0.  Any output may be NULL.
+ */
+void orc_populations(int lmax, int n, const double *E, const double *c,
+                     double *per_state, double *per_l, double *bound,
+                     double *ionised, double *norm)
+{
+    double b = 0.0, io = 0.0, nr = 0.0;
+    for (int l = 0; l <= lmax; ++l) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const long a = (long)l * n + i;
+            const double p = c[2 * a] * c[2 * a] + c[2 * a + 1] * c[2 * a + 1];
+            if (per_state) per_state[a] = p;
+            s += p;
+            if (E[a] < 0.0) b += p; else io += p;
+        }
+        if (per_l) per_l[l] = s;
+        nr += s;
+    }
+    if (bound) *bound = b;
+    if (ionised) *ionised = io;
+    if (norm) *norm = nr;
+}
+
+/* <a, b> = sum conj(a_j) b_j ; returns its imaginary part. */
+static double im_inner(long N, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (long q = 0; q < N; ++q) s += a[2 * q] * b[2 * q + 1] - a[2 * q + 1] * b[2 * q];
+    return s;
+}
+
+/*
+ * Backward through k = M(f) x = -i (E x + f D x) for real symmetric D:
+ * M^dagger = +i H, so g_x = i (E g_k + f D g_k); and
+ * dL/df = Re<g_k, -i D x> = Im<g_k, D x> = Im<D g_k, x>.
+ * Returns dL/df, adds g_x into gx (scaled by 1) and uses u as scratch (2N).
+ */
+static double back_deriv(int lmax, int n, const double *E, const double *U,
+                         double f, const double *gk, const double *x,
+                         double *gx, double *u)
+{
+    const long N = (long)(lmax + 1) * n;
+    orc_dmatvec(lmax, n, U, gk, u);
+    const double df = im_inner(N, u, x);
+    for (long a = 0; a < N; ++a) {
+        const double p = E[a] * gk[2 * a] + f * u[2 * a];
+        const double q = E[a] * gk[2 * a + 1] + f * u[2 * a + 1];
+        gx[2 * a] += -q;        /* i (p + i q) = -q + i p */
+        gx[2 * a + 1] += p;
+    }
+    return df;
+}
+
+/*
+ * Discrete adjoint (discretise-then-differentiate) of orc_rk4 / orc_taylor
+ * for the loss L = sum_j w_j |c_j(T)|^2.  Every state c_k is kept (no
+ * checkpointing: plain and slow); the stage vectors of step k are recomputed
+ * from c_k on the way back.  grad[] has the shape of F and receives dL/dF.
+ * scheme 0 = RK4, 1 = Taylor order K with the given hold.  c is in/out (final
+ * state), *loss receives L.
+ */
+void orc_adjoint(int lmax, int n, const double *E, const double *U, double *c,
+                 const double *F, int sps, double dt, long nsteps, int scheme,
+                 int K, int hold, const double *w, double *grad, double *loss)
+{
+    const long N = (long)(lmax + 1) * n;
+    const long nF = (sps == 2) ? 2 * nsteps + 1 : nsteps + 1;
+    for (long q = 0; q < nF; ++q) grad[q] = 0.0;
+    double *states = (double *)malloc(sizeof(double) * 2 * N * (nsteps + 1));
+    const int nst = (scheme == 0) ? 4 : K;
+    double *stg = (double *)malloc(sizeof(double) * 2 * N * (nst > 0 ? nst : 1));
+    double *work = (double *)malloc(sizeof(double) * 10 * N);
+    memcpy(states, c, sizeof(double) * 2 * N);
+    for (long k = 0; k < nsteps; ++k) {
+        double *ck = states + 2 * N * (k + 1);
+        memcpy(ck, states + 2 * N * k, sizeof(double) * 2 * N);
+        if (scheme == 0)
+            rk4_step(lmax, n, E, U, ck, orc_field_at(F, sps, k, 0), orc_field_at(F, sps, k, 1),
+                     orc_field_at(F, sps, k, 2), dt, work, NULL);
+        else
+            taylor_step(lmax, n, E, U, ck, taylor_field(F, sps, k, hold), dt, K, work, NULL);
+    }
+    const double *cT = states + 2 * N * nsteps;
+    double L = 0.0;
+    double *G = (double *)malloc(sizeof(double) * 2 * N);   /* dL/dc_k  */
+    double *gc = (double *)malloc(sizeof(double) * 2 * N);
+    double *gk = (double *)malloc(sizeof(double) * 2 * N);
+    double *gx = (double *)malloc(sizeof(double) * 2 * N);
+    double *u = (double *)malloc(sizeof(double) * 2 * N);
+    for (long a = 0; a < N; ++a) {
+        const double p = cT[2 * a] * cT[2 * a] + cT[2 * a + 1] * cT[2 * a + 1];
+        L += w[a] * p;
+        G[2 * a] = 2.0 * w[a] * cT[2 * a];
+        G[2 * a + 1] = 2.0 * w[a] * cT[2 * a + 1];
+    }
+    double *cc = (double *)malloc(sizeof(double) * 2 * N);
+    double *s = (double *)malloc(sizeof(double) * 2 * N);
+    for (long k = nsteps - 1; k >= 0; --k) {
+        memcpy(cc, states + 2 * N * k, sizeof(double) * 2 * N);
+        if (scheme == 0) {
+            /* recompute the stage inputs x1 = c_k, x2, x3, x4 of step k */
+            const double f0 = orc_field_at(F, sps, k, 0), fh = orc_field_at(F, sps, k, 1),
+                         f1 = orc_field_at(F, sps, k, 2);
+            rk4_step(lmax, n, E, U, cc, f0, fh, f1, dt, work, stg);
+            const double *x1 = stg, *x2 = stg + 2 * N, *x3 = stg + 4 * N, *x4 = stg + 6 * N;
+            double g0 = 0.0, gh = 0.0, g1 = 0.0;
+            /* c' = c + dt/6 k1 + dt/3 k2 + dt/3 k3 + dt/6 k4 */
+            memcpy(gc, G, sizeof(double) * 2 * N);
+            /* k4 = M(f1) x4 with x4 = c + dt k3 */
+            for (long q = 0; q < 2 * N; ++q) { gk[q] = dt / 6.0 * G[q]; gx[q] = 0.0; }
+            g1 += back_deriv(lmax, n, E, U, f1, gk, x4, gx, u);
+            for (long q = 0; q < 2 * N; ++q) { gc[q] += gx[q]; gk[q] = dt / 3.0 * G[q] + dt * gx[q]; gx[q] = 0.0; }
+            /* k3 = M(fh) x3 with x3 = c + dt/2 k2 */
+            gh += back_deriv(lmax, n, E, U, fh, gk, x3, gx, u);
+            for (long q = 0; q < 2 * N; ++q) { gc[q] += gx[q]; gk[q] = dt / 3.0 * G[q] + 0.5 * dt * gx[q]; gx[q] = 0.0; }
+            /* k2 = M(fh) x2 with x2 = c + dt/2 k1 */
+            gh += back_deriv(lmax, n, E, U, fh, gk, x2, gx, u);
+            for (long q = 0; q < 2 * N; ++q) { gc[q] += gx[q]; gk[q] = dt / 6.0 * G[q] + 0.5 * dt * gx[q]; gx[q] = 0.0; }
+            /* k1 = M(f0) c */
+            g0 += back_deriv(lmax, n, E, U, f0, gk, x1, gx, u);
+            for (long q = 0; q < 2 * N; ++q) G[q] = gc[q] + gx[q];
+            if (sps == 2) {
+                grad[2 * k] += g0; grad[2 * k + 1] += gh; grad[2 * k + 2] += g1;
+            } else {
+                grad[k] += g0 + 0.5 * gh; grad[k + 1] += g1 + 0.5 * gh;
+            }
+        } else {
+            /* recompute the Taylor terms T_0..T_{K-1} of step k */
+            const double fhold = taylor_field(F, sps, k, hold);
+            taylor_step(lmax, n, E, U, cc, fhold, dt, K, work, stg);
+            /* c' = sum_m T_m with T_m = (dt/m) M T_{m-1}: the cotangent of
+             * T_{m-1} is G + (dt/m) M^dagger (cotangent of T_m). */
+            double gf = 0.0;
+            memcpy(gk, G, sizeof(double) * 2 * N);   /* cotangent of T_K */
+            for (int m = K; m >= 1; --m) {
+                for (long q = 0; q < 2 * N; ++q) { s[q] = (dt / m) * gk[q]; gx[q] = 0.0; }
+                gf += back_deriv(lmax, n, E, U, fhold, s, stg + (long)(m - 1) * 2 * N, gx, u);
+                for (long q = 0; q < 2 * N; ++q) gk[q] = G[q] + gx[q];
+            }
+            memcpy(G, gk, sizeof(double) * 2 * N);
+            if (hold == 0) {
+                if (sps == 2) grad[2 * k] += gf; else grad[k] += gf;
+            } else {
+                if (sps == 2) grad[2 * k + 1] += gf;
+                else { grad[k] += 0.5 * gf; grad[k + 1] += 0.5 * gf; }
+            }
+        }
+    }
+    free(cc);
+    free(s);
+    memcpy(c, cT, sizeof(double) * 2 * N);
+    *loss = L;
+    free(states); free(stg); free(work); free(G); free(gc); free(gk); free(gx); free(u);
+}
