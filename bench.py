@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the propagator on the large single system.
+
+Workload: lmax=31, n=2000 (64000 amplitudes, 31 dense 2000x2000 dipole blocks
+with N(0,1)/sqrt(n) entries, seed 1), sin^2 pulse with 0.1 a.u. peak field,
+omega=0.5, dt=0.01, classic RK4.  A step is one RK4 step (4 block products
+with their stage updates).  Metric: RK4 amplitude-updates/s = N * steps /
+time, whole job.  Variants: float-float products (FP64-class accuracy, the
+headline), plain FP64 products, FP32 products; each reports its error
+against the FP64 variant over the same steps.
+
+--impl reference times the CPU oracle (plain FP64 C, OpenMP over blocks) on
+the host cores with the same workload, metric and unit.
+"""
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "RK4 amplitude-updates/s"
+UNIT = "amplitude-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--variants", default="df32,fp64,fp32")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound on the oracle timing sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload():
+    from paper_1201_6062_gb300 import inputs
+    cfg = inputs.large_system()
+    return cfg
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples over the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.25)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = list(csv.reader(io.StringIO(self.file.read())))
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        return dist, rank, ws, local
+    return None, 0, 1, 0
+
+
+def cpu_baseline(cfg, seconds, E=None, U=None):
+    """The oracle as it stands on the host cores: RK4 steps of the same system
+    until `seconds` have elapsed (at least one step)."""
+    import oracle
+    from paper_1201_6062_gb300 import inputs
+    lmax, n, dt = cfg["lmax"], cfg["n"], cfg["dt"]
+    if E is None:
+        E = inputs.energies(lmax, n)
+        U = inputs.dipoles(lmax, n, cfg["seed"])
+    c = inputs.ground_state(lmax, n)
+    F = inputs.field_samples(cfg["E0"], cfg["omega"], dt, 4096, 1)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        c, _ = oracle.rk4(lmax, n, E, U, c, F[steps:steps + 2], dt, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 4096:
+            break
+    N = (lmax + 1) * n
+    return {"value": N * steps / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d RK4 steps of the lmax=31 n=2000 system (%.1f s)" % (steps, el)}
+
+
+def run_reference(args):
+    dist, rank, ws, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    from paper_1201_6062_gb300 import inputs
+    oracle.build()
+    cfg = workload()
+    lmax, n, dt = cfg["lmax"], cfg["n"], cfg["dt"]
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, cfg["seed"])
+    N = (lmax + 1) * n
+    F = inputs.field_samples(cfg["E0"], cfg["omega"], dt, args.warmup + args.steps + 1, 1)
+    c = inputs.ground_state(lmax, n)
+    for k in range(args.warmup):
+        c, _ = oracle.rk4(lmax, n, E, U, c, F[k:k + 2], dt, 1)
+    t0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        c, _ = oracle.rk4(lmax, n, E, U, c, F[k:k + 2], dt, 1)
+    el = time.perf_counter() - t0
+    value = N * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(cfg, "oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": "%d RK4 steps of the lmax=31 n=2000 system" % args.steps},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def config_dict(cfg, variant):
+    return {"workload": "single large system lmax=31 n=2000 (64000 amplitudes), RK4, dt=0.01, E0=0.1 a.u., omega=0.5",
+            "lmax": cfg["lmax"], "n": cfg["n"], "amplitudes": (cfg["lmax"] + 1) * cfg["n"], "scheme": "rk4",
+            "dt": cfg["dt"], "variant": variant,
+            "l2": "no flush: each step streams every dipole block (496-992 MB) through the 129 MB L2"}
+
+
+def run_ours(args):
+    import torch
+    from paper_1201_6062_gb300 import build
+    build.build()
+    from paper_1201_6062_gb300 import inputs, tdse
+
+    dist, rank, ws, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = workload()
+    lmax, n, dt = cfg["lmax"], cfg["n"], cfg["dt"]
+    N = (lmax + 1) * n
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, cfg["seed"])
+    W, K = args.warmup, args.steps
+    F = inputs.field_samples(cfg["E0"], cfg["omega"], dt, W + K, 1)
+    c0 = inputs.ground_state(lmax, n)
+    variants = [v for v in args.variants.split(",") if v]
+    primary = variants[0]
+    hbm_peak, peak_kind = peaks()
+    res = {}
+    finals = {}
+    clocks = None
+    for prec in variants:
+        H = tdse.Hamiltonian(E, U, lmax, n, prec)
+        c = torch.from_numpy(c0.copy()).to(dev)
+        f_warm = torch.from_numpy(F[:W + 1].copy()).to(dev)
+        f_time = torch.from_numpy(F[W:W + K + 1].copy()).to(dev)
+        H.propagate(c, f_warm, dt, W)
+        torch.cuda.synchronize()
+        H.profile(True)
+        H.profile_read()
+        sampler = ClockSampler(local) if prec == primary else None
+        if sampler:
+            sampler.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        H.propagate(c, f_time, dt, K)
+        e1.record()
+        e1.synchronize()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        if sampler:
+            clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        mv_ms, mv_n, launches = H.profile_read()
+        H.profile(False)
+        ub = {"fp64": 8, "df32": 8, "fp32": 4}[prec]
+        xb = {"fp64": 16, "df32": 16, "fp32": 8}[prec]
+        alg_bytes = lmax * n * n * ub + N * (xb + 16)
+        mv_avg = mv_ms / max(mv_n, 1)
+        res[prec] = {
+            "value": ws * N * K / (ms / 1e3), "ms_per_step": ms / K, "mv_ms_avg": mv_avg,
+            "mv_launches": mv_n, "gpu_launches": launches,
+            "mv_gbs": alg_bytes / (mv_avg / 1e3) / 1e9,
+            "mv_tflops": 8.0 * lmax * n * n / (mv_avg / 1e3) / 1e12,
+            "alg_bytes_per_launch": alg_bytes,
+        }
+        finals[prec] = c.cpu().numpy()
+        H.close()
+        del c
+        torch.cuda.empty_cache()
+
+    ref = finals.get("fp64")
+    for prec in variants:
+        if ref is not None:
+            res[prec]["err_vs_fp64"] = float(np.linalg.norm(finals[prec] - ref) / np.linalg.norm(ref))
+        res[prec]["norm_drift"] = float(abs(np.vdot(finals[prec], finals[prec]).real - 1.0))
+
+    p = res[primary]
+    if primary == "fp64":
+        roof = {"bound": "alu", "achieved": p["mv_tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": p["mv_tflops"] / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": p["mv_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": p["mv_gbs"] / hbm_peak, "traffic": None, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+    roof["kernel"] = "mv_kernel<%s>" % primary
+    roof["alg_bytes_per_launch"] = p["alg_bytes_per_launch"]
+
+    e2e = None
+    if not args.no_e2e:
+        H = tdse.Hamiltonian(E, U, lmax, n, primary)
+        ch = torch.from_numpy(c0.copy()).pin_memory()
+        fh = torch.from_numpy(F[:K + 1].copy()).pin_memory()
+        H.propagate_host(ch, torch.from_numpy(F[:2].copy()).pin_memory(), dt, 1)   # warm the host path
+        ch.copy_(torch.from_numpy(c0))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H.propagate_host(ch, fh, dt, K)
+        el = time.perf_counter() - t0
+        H.close()
+        e2e = {"value": ws * N * K / el, "unit": UNIT, "h2d_bytes_per_step": (N * 16 + (K + 1) * 8) / K,
+               "d2h_bytes_per_step": N * 16 / K,
+               "note": "tdse_propagate_host: pinned host c and field in, K steps, c out, synchronised"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg, args.cpu_seconds, E, U)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": p["value"], "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": p["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"df32": "f32x2 (float-float products, FP64 state)", "fp64": "f64",
+                      "fp32": "f32 products, FP64 state"}[primary],
+            "data": "synthetic", "config": config_dict(cfg, primary),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": p["gpu_launches"],
+            "variants": res,
+        }
+        print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

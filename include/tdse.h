@@ -1,0 +1,247 @@
+/*
+ * tdse.h — C ABI of the GB300 (sm_103a) propagator for the laser-driven
+ * hydrogen time-dependent Schrödinger equation in a field-free eigenstate
+ * basis (Ó Broin & Nikolopoulos, "An OpenCL implementation for the solution
+ * of TDSE on GPU and CPU architectures", arXiv:1201.6062).
+ *
+ * The ODE (paper Sec. 3, Eq. "tdse_ode_c"; Sec. 4, Eq. "ode"):
+ *     dc/dt = -i H(t) c,   H(t) = diag(E) + f(t) D,
+ * with c the complex amplitudes of N = (lmax+1)*n eigenstates, grouped into
+ * angular-momentum blocks l = 0..lmax of n states each (block l holds
+ * amplitudes [l*n, (l+1)*n)).  By the dipole selection rule (Sec. 3.1,
+ * Fig. "Matrix") D couples only neighbouring blocks: D_{l,l+1} = U_l is a
+ * dense real n x n block and D_{l+1,l} = U_l^T (Sec. 5: only the upper blocks
+ * are stored).  f(t) is the electric-field sample (length gauge, Sec. 5).
+ *
+ * Common conventions
+ *  - Complex vectors are interleaved (re, im) FP64 pairs, i.e. the memory of
+ *    a complex128 array.  c[2*a] = Re c_a, c[2*a+1] = Im c_a.
+ *  - Pointers documented "device" must be CUDA device memory of the current
+ *    device, 16-byte aligned; "host" pointers are ordinary host memory.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it and the call returns without waiting, except where noted.
+ *  - Field samples (the paper does not fix this; the reading used here):
+ *      samples_per_step = 1: field[k] = f(t0 + k dt), k = 0..nsteps; the
+ *        value at a half step is the mean of its two neighbours;
+ *      samples_per_step = 2: field[h] = f(t0 + h dt/2), h = 0..2*nsteps.
+ *  - Every call returns a tdse_status and never throws.  On failure the
+ *    output buffers are unspecified and tdse_last_error() describes the cause
+ *    (thread-local string, valid until the next call on the same thread).
+ *  - A context is not thread-safe; distinct contexts may be used from
+ *    distinct threads.
+ */
+#ifndef TDSE_H
+#define TDSE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TDSE_OK = 0,
+    TDSE_EINVAL = 1,    /* bad argument (NULL, size, enum, misaligned pointer) */
+    TDSE_ENOMEM = 2,    /* device or host allocation failed                    */
+    TDSE_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed         */
+    TDSE_ETIMEOUT = 4,  /* a bounded device-side wait gave up                  */
+    TDSE_ENOTSUP = 5    /* valid request this build does not support           */
+} tdse_status;
+
+typedef enum {
+    TDSE_RK4 = 0,       /* classic 4-stage Runge-Kutta (App. B, "RKFinal"/"RKDeriv") */
+    TDSE_TAYLOR = 1     /* truncated Taylor series (App. B, Eq. "taylor")             */
+} tdse_scheme;
+
+typedef enum {
+    TDSE_HOLD_LEFT = 0, /* Taylor: H frozen at t_k (the paper's "known time t")  */
+    TDSE_HOLD_MID = 1   /* Taylor: H frozen at t_k + dt/2                        */
+} tdse_hold;
+
+/*
+ * Arithmetic of the dipole-block products.  The state, the diagonal part
+ * E o c, the stage/term updates, norms and populations are FP64 in every
+ * mode.
+ *   TDSE_FP64   U stored FP64, products and sums in FP64.
+ *   TDSE_FP32   U stored FP32 (half the bytes), products and sums in FP32,
+ *               each block result rounded into the FP64 state.
+ *   TDSE_DF32   U stored as an FP32 (hi, lo) pair, products and sums in
+ *               float-float arithmetic (about 44 significant bits) on the
+ *               FP32 pipe; FP64-class accuracy without FP64 multiplies.
+ *   TDSE_BF16X3 batched paths only: U and the batched state split into
+ *               bf16 (hi, lo) pairs, three tensor-core products with FP32
+ *               accumulation.
+ */
+typedef enum {
+    TDSE_FP64 = 0,
+    TDSE_FP32 = 1,
+    TDSE_DF32 = 2,
+    TDSE_BF16X3 = 3
+} tdse_precision;
+
+typedef struct tdse_ctx tdse_ctx;            /* one Hamiltonian (E, U) resident on the GPU */
+
+/* Version of this ABI (major*10000 + minor*100 + patch). */
+int tdse_version(void);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char *tdse_last_error(void);
+
+/*
+ * tdse_create — upload one Hamiltonian (paper Sec. 5, storage: each diagonal
+ * block E_L followed by the superdiagonal block D_L, lower blocks implicit).
+ *   energies       host, FP64 [(lmax+1)*n], block l contiguous.
+ *   dipole_blocks  host, FP64 [lmax][n][n], row-major U_l = D_{l,l+1};
+ *                  may be NULL when lmax == 0.
+ *   lmax           >= 0; n >= 1; n <= 4096.
+ *   prec           arithmetic of the dipole products (see tdse_precision).
+ *   out            receives the new context; the caller owns it and frees it
+ *                  with tdse_destroy.
+ * The host arrays are copied (and converted to the storage format of `prec`)
+ * into device memory owned by the context; they may be freed on return.
+ * Synchronous.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+tdse_status tdse_create(const double *energies, const double *dipole_blocks,
+                        int lmax, int n, tdse_precision prec, tdse_ctx **out);
+
+/* Frees the context and its device memory (after synchronising its work). */
+void tdse_destroy(tdse_ctx *ctx);
+
+/* Number of amplitudes N = (lmax+1)*n of the context (0 if ctx is NULL). */
+long tdse_size(const tdse_ctx *ctx);
+
+/*
+ * tdse_hmatvec — one Hamiltonian-vector product (paper Sec. 4, the block
+ * form of H C): y = -i H(f) x  (scale_by_minus_i != 0) or y = H(f) x.
+ *   x, y   device, complex [N]; must not alias.
+ * Asynchronous on `stream`.  Errors: EINVAL, ECUDA.
+ */
+tdse_status tdse_hmatvec(tdse_ctx *ctx, double f, const double *x, double *y,
+                         int scale_by_minus_i, void *stream);
+
+/*
+ * tdse_propagate — advance c over nsteps steps of dt (paper Sec. 4 and
+ * App. B): each RK4 stage or Taylor term is one Hamiltonian-vector product
+ * fused with its stage update.
+ *   c               device, complex [N], in: c(t0), out: c(t0 + nsteps dt).
+ *   field           device, FP64 [samples_per_step*nsteps + 1] (see above).
+ *   samples_per_step 1 or 2.
+ *   dt              step (> 0 or < 0, finite); nsteps >= 0.
+ *   scheme          TDSE_RK4 or TDSE_TAYLOR.
+ *   taylor_order    K >= 1 (Taylor only; ignored for RK4).
+ *   taylor_hold     tdse_hold (Taylor only).
+ * Scratch vectors live in the context.  Asynchronous on `stream`; the
+ * context must not be used on another stream concurrently.
+ * Errors: EINVAL, ECUDA.
+ */
+tdse_status tdse_propagate(tdse_ctx *ctx, double *c, const double *field,
+                           int samples_per_step, double dt, long nsteps,
+                           tdse_scheme scheme, int taylor_order, int taylor_hold,
+                           void *stream);
+
+/*
+ * tdse_propagate_host — tdse_propagate on HOST buffers: copies c and field
+ * to the device, propagates, copies c back and synchronises `stream`.
+ *   c_host      host, complex [N], in/out.
+ *   field_host  host, FP64 [samples_per_step*nsteps + 1].
+ * Errors: as tdse_propagate, plus ENOMEM.
+ */
+tdse_status tdse_propagate_host(tdse_ctx *ctx, double *c_host, const double *field_host,
+                                int samples_per_step, double dt, long nsteps,
+                                tdse_scheme scheme, int taylor_order, int taylor_hold,
+                                void *stream);
+
+/*
+ * tdse_norm — out[b] = sum_a |c[b][a]|^2 for b < B, FP64 with a fixed
+ * reduction order (bitwise reproducible).  Unitarity is the error measure of
+ * paper Sec. 5.1.
+ *   c    device, complex [B][N];  out  device, FP64 [B].
+ * Errors: EINVAL, ECUDA.
+ */
+tdse_status tdse_norm(tdse_ctx *ctx, const double *c, int B, double *out, void *stream);
+
+/*
+ * tdse_populations — populations after the pulse (paper Sec. 5: the
+ * continuum population is the ionisation).  For each of B states:
+ *   per_state [B][N]   |c_a|^2                     (device, may be NULL)
+ *   per_l     [B][lmax+1] sum over each block      (device, may be NULL)
+ *   bound     [B]  sum over E_a <  0               (device, may be NULL)
+ *   ionised   [B]  sum over E_a >= 0               (device, may be NULL)
+ * FP64, fixed reduction order.  Errors: EINVAL, ECUDA.
+ */
+tdse_status tdse_populations(tdse_ctx *ctx, const double *c, int B, double *per_state,
+                             double *per_l, double *bound, double *ionised, void *stream);
+
+/*
+ * tdse_propagate_batch — B independent pulses sharing the context's
+ * Hamiltonian (a pulse sweep).  The B states are advanced together so that
+ * each dipole block is read once per stage for all of them (block GEMMs
+ * U_l [X_{l+1}] and U_l^T [X_l] with X the n x 2B real matrix of the states'
+ * real and imaginary parts).
+ *   c      device, complex [B][N], in/out.
+ *   field  device, FP64 [B][samples_per_step*nsteps + 1].
+ * Other arguments as tdse_propagate.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, int B,
+                                 int samples_per_step, double dt, long nsteps,
+                                 tdse_scheme scheme, int taylor_order, int taylor_hold,
+                                 void *stream);
+
+/*
+ * tdse_adjoint — gradient of L = sum_a w_a |c_a(T)|^2 with respect to every
+ * field sample, by the exact discrete adjoint of tdse_propagate (the paper
+ * has no adjoint; discretise-then-differentiate).  The forward pass stores
+ * c every `checkpoint_every` steps; the backward pass recomputes each
+ * segment's stage vectors from its checkpoint and runs the costate
+ * recursion g_x = (-i H)^dagger g_k backwards.
+ *   c0         device, complex [N] (not modified).
+ *   field      device, FP64 [samples_per_step*nsteps + 1].
+ *   weights    device, FP64 [N] (w_a).
+ *   checkpoint_every  >= 1.
+ *   grad_field device, FP64, same length as field (overwritten).
+ *   c_final    device, complex [N] or NULL: receives c(T).
+ *   loss       device, FP64 [1] or NULL: receives L.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field,
+                         int samples_per_step, double dt, long nsteps, tdse_scheme scheme,
+                         int taylor_order, int taylor_hold, const double *weights,
+                         int checkpoint_every, double *grad_field, double *c_final,
+                         double *loss, void *stream);
+
+/*
+ * Kernel tracing.  While enabled, every block-product launch of the context
+ * is bracketed by a pair of CUDA events on its stream, and every kernel the
+ * context launches is counted.  tdse_profile_read waits for the recorded
+ * events, returns the summed device time of the block-product launches (ms),
+ * their number and the number of all kernels launched since the last read,
+ * and resets the counters.  Any output pointer may be NULL.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+tdse_status tdse_profile_enable(tdse_ctx *ctx, int on);
+tdse_status tdse_profile_read(tdse_ctx *ctx, double *mv_ms, long *mv_launches, long *kernel_launches);
+
+/*
+ * Uneven batches: several contexts of different (lmax, n) advanced together,
+ * one kernel launch per stage for all of them (rows of every system are split
+ * evenly over the GPU's SMs).  All contexts must share one precision.
+ */
+typedef struct tdse_group tdse_group;
+
+/* systems: host array of `count` contexts (borrowed: they must outlive the
+ * group).  Errors: EINVAL, ENOMEM, ECUDA. */
+tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **out);
+void tdse_group_destroy(tdse_group *g);
+
+/*
+ * c_ptrs[s]      device, complex [N_s] state of system s (in/out).
+ * field_ptrs[s]  device, FP64 [samples_per_step*nsteps + 1] field of system s.
+ * Both arrays are host arrays of `count` device pointers.  RK4 only.
+ * Errors: EINVAL, ECUDA, ENOTSUP.
+ */
+tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs,
+                                 const double *const *field_ptrs, int samples_per_step,
+                                 double dt, long nsteps, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDSE_H */

@@ -1,0 +1,472 @@
+// C ABI of the propagator (declarations and contracts in include/tdse.h).
+// Host orchestration only: argument checks, device storage, the work plan and
+// the launch sequence.  Every arithmetic step runs in the kernels.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tdse.h"
+#include "kernels.h"
+#include "plan.h"
+
+using tdse::SysDesc;
+using tdse::Seg;
+
+static thread_local std::string g_err;
+
+static tdse_status fail(tdse_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(TDSE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Device memory owned by a context or group; freed by the destructor.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    cudaError_t ensure(size_t nbytes)
+    {
+        if (nbytes <= bytes && p) return cudaSuccess;
+        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        cudaError_t e = cudaMalloc(&p, nbytes ? nbytes : 16);
+        if (e == cudaSuccess) bytes = nbytes;
+        return e;
+    }
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Launch plan of the block mat-vec for one or several systems.
+struct MvPlan {
+    tdse::MvCfg cfg{};
+    int grid = 0;
+    int nblk = 0;          // epilogue blocks
+    DevBuf segs, cta_off, blk;
+};
+
+struct tdse_ctx {
+    int lmax = 0, n = 0, N = 0, ld = 0, prec = 0;
+    long long bstride = 0;
+    DevBuf U, E, R, P, x, acc, xq, sb, sys;
+    DevBuf part;                       // populations scratch
+    DevBuf hc, hfield;                 // device copies for the host-buffer entry point
+    MvPlan plan;
+    SysDesc desc{};                    // host copy of the descriptor (static fields filled)
+    SysDesc *stage = nullptr;          // pinned staging for descriptor uploads
+    cudaEvent_t stage_ev = nullptr;
+    bool stage_pending = false;
+    int nslots = 0;
+    // tracing
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
+    size_t prof_used = 0;               // events in use
+    long launches = 0;
+    ~tdse_ctx()
+    {
+        cudaDeviceSynchronize();
+        if (stage) cudaFreeHost(stage);
+        if (stage_ev) cudaEventDestroy(stage_ev);
+        for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    }
+};
+
+static int elem_bytes(int prec) { return prec == TDSE_FP32 ? 4 : 8; }
+
+static int sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    return sms;
+}
+
+// Build the mat-vec plan for the given systems and upload it.
+static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std::vector<int> &n, MvPlan &mp,
+                              tdse::Plan &plan)
+{
+    int nmax = 1;
+    long long rows = 0, amps = 0;
+    for (size_t s = 0; s < n.size(); ++s) {
+        nmax = n[s] > nmax ? n[s] : nmax;
+        rows += (long long)lmax[s] * n[s];
+    }
+    if (!tdse::mv_config(prec, nmax, &mp.cfg)) return fail(TDSE_ENOTSUP, "n=%d exceeds the supported maximum", nmax);
+    int G = sm_count() * tdse::mv_ctas_per_sm(prec, mp.cfg);
+    if (rows < G) G = (int)(rows > 0 ? rows : 1);
+    tdse::make_plan(G, lmax, n, 32, plan);
+    mp.grid = rows > 0 ? G : 0;
+    std::vector<Seg> segs(plan.segs.size());
+    for (size_t i = 0; i < segs.size(); ++i) {
+        const tdse::PlanSeg &p = plan.segs[i];
+        segs[i] = Seg{p.sys, p.l, p.i0, p.i1, p.slot};
+    }
+    std::vector<int2> blk;
+    for (size_t s = 0; s < n.size(); ++s) {
+        const long long N = (long long)(lmax[s] + 1) * n[s];
+        amps += N;
+        for (long long a = 0; a < N; a += 256) blk.push_back(make_int2((int)s, (int)a));
+    }
+    mp.nblk = (int)blk.size();
+    CUDA_TRY(mp.segs.ensure(sizeof(Seg) * (segs.empty() ? 1 : segs.size())));
+    CUDA_TRY(mp.cta_off.ensure(sizeof(int) * plan.cta_off.size()));
+    CUDA_TRY(mp.blk.ensure(sizeof(int2) * (blk.empty() ? 1 : blk.size())));
+    if (!segs.empty()) CUDA_TRY(cudaMemcpy(mp.segs.p, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(mp.cta_off.p, plan.cta_off.data(), sizeof(int) * plan.cta_off.size(), cudaMemcpyHostToDevice));
+    if (!blk.empty()) CUDA_TRY(cudaMemcpy(mp.blk.p, blk.data(), sizeof(int2) * blk.size(), cudaMemcpyHostToDevice));
+    return TDSE_OK;
+}
+
+extern "C" {
+
+int tdse_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+const char *tdse_last_error(void) { return g_err.c_str(); }
+
+long tdse_size(const tdse_ctx *ctx) { return ctx ? (long)ctx->N : 0; }
+
+tdse_status tdse_create(const double *energies, const double *dipole_blocks, int lmax, int n, tdse_precision prec,
+                        tdse_ctx **out)
+{
+    g_err.clear();
+    if (!out) return fail(TDSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!energies) return fail(TDSE_EINVAL, "energies is NULL");
+    if (lmax < 0 || n < 1 || n > 4096) return fail(TDSE_EINVAL, "need lmax >= 0 and 1 <= n <= 4096 (lmax=%d n=%d)", lmax, n);
+    if (lmax > 0 && !dipole_blocks) return fail(TDSE_EINVAL, "dipole_blocks is NULL with lmax=%d", lmax);
+    if (prec != TDSE_FP64 && prec != TDSE_FP32 && prec != TDSE_DF32)
+        return fail(TDSE_ENOTSUP, "precision %d is only available on batched paths", (int)prec);
+    tdse_ctx *c = new (std::nothrow) tdse_ctx();
+    if (!c) return fail(TDSE_ENOMEM, "host allocation failed");
+    c->lmax = lmax; c->n = n; c->N = (lmax + 1) * n; c->prec = prec;
+    c->ld = (n + 3) & ~3;
+    const int eb = elem_bytes(prec);
+    long long blk_elems = (long long)n * c->ld;
+    const long long align = 256 / eb;
+    c->bstride = (blk_elems + align - 1) / align * align;
+    tdse_status st = TDSE_OK;
+    auto bail = [&](tdse_status s) { delete c; return s; };
+#define CTRY(call)                                                                                \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return bail(fail(TDSE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_))); \
+    } while (0)
+    // Dipole blocks in the storage format of the precision (converted on the host).
+    const size_t ubytes = (size_t)(lmax > 0 ? lmax : 1) * (size_t)c->bstride * eb;
+    CTRY(c->U.ensure(ubytes));
+    CTRY(cudaMemset(c->U.p, 0, ubytes));
+    if (lmax > 0) {
+        std::vector<char> host((size_t)c->bstride * eb, 0);
+        for (int l = 0; l < lmax; ++l) {
+            std::memset(host.data(), 0, host.size());
+            const double *src = dipole_blocks + (size_t)l * n * n;
+            for (int i = 0; i < n; ++i) {
+                for (int j = 0; j < n; ++j) {
+                    const double v = src[(size_t)i * n + j];
+                    const size_t q = (size_t)i * c->ld + j;
+                    if (prec == TDSE_FP64) {
+                        reinterpret_cast<double *>(host.data())[q] = v;
+                    } else if (prec == TDSE_FP32) {
+                        reinterpret_cast<float *>(host.data())[q] = (float)v;
+                    } else {
+                        const float h = (float)v;
+                        const float lo = (float)(v - (double)h);
+                        reinterpret_cast<float *>(host.data())[2 * q] = h;
+                        reinterpret_cast<float *>(host.data())[2 * q + 1] = lo;
+                    }
+                }
+            }
+            CTRY(cudaMemcpy((char *)c->U.p + (size_t)l * c->bstride * eb, host.data(), host.size(),
+                            cudaMemcpyHostToDevice));
+        }
+    }
+    CTRY(c->E.ensure(sizeof(double) * c->N));
+    CTRY(cudaMemcpy(c->E.p, energies, sizeof(double) * c->N, cudaMemcpyHostToDevice));
+    tdse::Plan plan;
+    st = build_plan(prec, std::vector<int>{lmax}, std::vector<int>{n}, c->plan, plan);
+    if (st != TDSE_OK) return bail(st);
+    c->nslots = plan.nslots[0];
+    CTRY(c->R.ensure(sizeof(double2) * c->N));
+    CTRY(cudaMemset(c->R.p, 0, sizeof(double2) * c->N));
+    CTRY(c->P.ensure(sizeof(double2) * (size_t)(c->nslots > 0 ? c->nslots : 1) * n));
+    CTRY(c->x.ensure(sizeof(double2) * c->N));
+    CTRY(c->acc.ensure(sizeof(double2) * c->N));
+    CTRY(c->xq.ensure((size_t)16 * c->N));
+    CTRY(c->sb.ensure(sizeof(int) * (lmax + 1)));
+    CTRY(cudaMemcpy(c->sb.p, plan.sb[0].data(), sizeof(int) * (lmax + 1), cudaMemcpyHostToDevice));
+    CTRY(c->sys.ensure(sizeof(SysDesc)));
+    CTRY(cudaMallocHost((void **)&c->stage, sizeof(SysDesc)));
+    CTRY(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
+#undef CTRY
+    SysDesc &d = c->desc;
+    d.U = c->U.p; d.bstride = c->bstride; d.ld = c->ld; d.n = n; d.lmax = lmax; d.N = c->N;
+    d.E = c->E.as<double>(); d.R = c->R.as<double2>(); d.P = c->P.as<double2>(); d.sb = c->sb.as<int>();
+    d.c = nullptr; d.x = c->x.as<double2>(); d.acc = c->acc.as<double2>(); d.xq = c->xq.p; d.field = nullptr;
+    *out = c;
+    return TDSE_OK;
+}
+
+void tdse_destroy(tdse_ctx *ctx) { delete ctx; }
+
+// Upload a descriptor through the pinned staging slot (stream ordered).
+static tdse_status stage_desc(tdse_ctx *c, const SysDesc &d, cudaStream_t s)
+{
+    if (c->stage_pending) CUDA_TRY(cudaEventSynchronize(c->stage_ev));
+    *c->stage = d;
+    CUDA_TRY(cudaMemcpyAsync(c->sys.p, c->stage, sizeof(SysDesc), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaEventRecord(c->stage_ev, s));
+    c->stage_pending = true;
+    return TDSE_OK;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Event pair for one traced launch (grown on demand, reused after each read).
+static tdse_status prof_pair(tdse_ctx *c, cudaEvent_t *e0, cudaEvent_t *e1)
+{
+    while (c->prof_used + 2 > c->prof_ev.size()) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        c->prof_ev.push_back(e);
+    }
+    *e0 = c->prof_ev[c->prof_used];
+    *e1 = c->prof_ev[c->prof_used + 1];
+    c->prof_used += 2;
+    return TDSE_OK;
+}
+
+static tdse_status mv_and_epi(tdse_ctx *c, tdse::EpiArgs a, cudaStream_t s)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool traced = c->prof_on && c->plan.grid > 0;
+    if (traced) {
+        tdse_status st = prof_pair(c, &e0, &e1);
+        if (st != TDSE_OK) return st;
+        CUDA_TRY(cudaEventRecord(e0, s));
+    }
+    CUDA_TRY(tdse::launch_mv(c->prec, c->plan.cfg, c->plan.grid, c->sys.as<SysDesc>(), c->plan.segs.as<Seg>(),
+                             c->plan.cta_off.as<int>(), s));
+    if (traced) CUDA_TRY(cudaEventRecord(e1, s));
+    CUDA_TRY(tdse::launch_epi(c->prec, c->plan.nblk, c->plan.blk.as<int2>(), c->sys.as<SysDesc>(), a, s));
+    c->launches += (c->plan.grid > 0 ? 1 : 0) + (c->plan.nblk > 0 ? 1 : 0);
+    return TDSE_OK;
+}
+
+tdse_status tdse_hmatvec(tdse_ctx *ctx, double f, const double *x, double *y, int scale_by_minus_i, void *stream)
+{
+    g_err.clear();
+    if (!ctx || !x || !y) return fail(TDSE_EINVAL, "NULL argument");
+    if (!aligned16(x) || !aligned16(y)) return fail(TDSE_EINVAL, "x and y must be 16-byte aligned");
+    if (x == y) return fail(TDSE_EINVAL, "x and y must not alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    SysDesc d = ctx->desc;
+    d.x = (double2 *)const_cast<double *>(x);
+    d.acc = (double2 *)y;
+    tdse_status st = stage_desc(ctx, d, s);
+    if (st != TDSE_OK) return st;
+    CUDA_TRY(tdse::launch_prep(ctx->prec, ctx->plan.nblk, ctx->plan.blk.as<int2>(), ctx->sys.as<SysDesc>(), 1, s));
+    ctx->launches += 1;
+    tdse::EpiArgs a{};
+    a.mode = scale_by_minus_i ? tdse::EPI_MIHX : tdse::EPI_HX;
+    a.fval = f;
+    return mv_and_epi(ctx, a, s);
+}
+
+static tdse_status check_prop_args(tdse_ctx *ctx, const double *c, const double *field, int sps, double dt,
+                                   long nsteps, tdse_scheme scheme, int order, int hold)
+{
+    if (!ctx || !c || !field) return fail(TDSE_EINVAL, "NULL argument");
+    if (!aligned16(c)) return fail(TDSE_EINVAL, "c must be 16-byte aligned");
+    if (sps != 1 && sps != 2) return fail(TDSE_EINVAL, "samples_per_step must be 1 or 2 (got %d)", sps);
+    if (!(dt == dt) || dt == 0.0 || dt > 1e300 || dt < -1e300) return fail(TDSE_EINVAL, "dt must be finite and nonzero");
+    if (nsteps < 0) return fail(TDSE_EINVAL, "nsteps must be >= 0");
+    if (scheme != TDSE_RK4 && scheme != TDSE_TAYLOR) return fail(TDSE_EINVAL, "unknown scheme %d", (int)scheme);
+    if (scheme == TDSE_TAYLOR && (order < 1 || order > 64)) return fail(TDSE_EINVAL, "taylor_order must be in 1..64");
+    if (scheme == TDSE_TAYLOR && hold != TDSE_HOLD_LEFT && hold != TDSE_HOLD_MID)
+        return fail(TDSE_EINVAL, "unknown taylor_hold %d", hold);
+    return TDSE_OK;
+}
+
+static tdse_status propagate_impl(tdse_ctx *ctx, double *c, const double *field, int sps, double dt, long nsteps,
+                                  tdse_scheme scheme, int order, int hold, cudaStream_t s)
+{
+    SysDesc d = ctx->desc;
+    d.c = (double2 *)c;
+    d.field = field;
+    tdse_status st = stage_desc(ctx, d, s);
+    if (st != TDSE_OK) return st;
+    if (nsteps == 0) return TDSE_OK;
+    CUDA_TRY(tdse::launch_prep(ctx->prec, ctx->plan.nblk, ctx->plan.blk.as<int2>(), ctx->sys.as<SysDesc>(), 0, s));
+    ctx->launches += 1;
+    tdse::EpiArgs a{};
+    a.sps = sps;
+    a.dt = dt;
+    a.order = order;
+    a.hold = hold;
+    for (long k = 0; k < nsteps; ++k) {
+        a.k = k;
+        if (scheme == TDSE_RK4) {
+            a.mode = tdse::EPI_RK4;
+            for (int stg = 0; stg < 4; ++stg) {
+                a.stage = stg;
+                st = mv_and_epi(ctx, a, s);
+                if (st != TDSE_OK) return st;
+            }
+        } else {
+            a.mode = tdse::EPI_TAYLOR;
+            for (int m = 1; m <= order; ++m) {
+                a.stage = m;
+                st = mv_and_epi(ctx, a, s);
+                if (st != TDSE_OK) return st;
+            }
+        }
+    }
+    return TDSE_OK;
+}
+
+tdse_status tdse_propagate(tdse_ctx *ctx, double *c, const double *field, int samples_per_step, double dt,
+                           long nsteps, tdse_scheme scheme, int taylor_order, int taylor_hold, void *stream)
+{
+    g_err.clear();
+    tdse_status st = check_prop_args(ctx, c, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold);
+    if (st != TDSE_OK) return st;
+    return propagate_impl(ctx, c, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold,
+                          (cudaStream_t)stream);
+}
+
+tdse_status tdse_propagate_host(tdse_ctx *ctx, double *c_host, const double *field_host, int samples_per_step,
+                                double dt, long nsteps, tdse_scheme scheme, int taylor_order, int taylor_hold,
+                                void *stream)
+{
+    g_err.clear();
+    if (!ctx || !c_host || !field_host) return fail(TDSE_EINVAL, "NULL argument");
+    if (samples_per_step != 1 && samples_per_step != 2) return fail(TDSE_EINVAL, "samples_per_step must be 1 or 2");
+    if (nsteps < 0) return fail(TDSE_EINVAL, "nsteps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t cb = sizeof(double2) * ctx->N;
+    const size_t fb = sizeof(double) * ((size_t)samples_per_step * nsteps + 1);
+    CUDA_TRY(ctx->hc.ensure(cb));
+    CUDA_TRY(ctx->hfield.ensure(fb));
+    CUDA_TRY(cudaMemcpyAsync(ctx->hc.p, c_host, cb, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(ctx->hfield.p, field_host, fb, cudaMemcpyHostToDevice, s));
+    tdse_status st = check_prop_args(ctx, ctx->hc.as<double>(), ctx->hfield.as<double>(), samples_per_step, dt, nsteps,
+                                     scheme, taylor_order, taylor_hold);
+    if (st != TDSE_OK) return st;
+    st = propagate_impl(ctx, ctx->hc.as<double>(), ctx->hfield.as<double>(), samples_per_step, dt, nsteps, scheme,
+                        taylor_order, taylor_hold, s);
+    if (st != TDSE_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(c_host, ctx->hc.p, cb, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return TDSE_OK;
+}
+
+tdse_status tdse_populations(tdse_ctx *ctx, const double *c, int B, double *per_state, double *per_l, double *bound,
+                             double *ionised, void *stream)
+{
+    g_err.clear();
+    if (!ctx || !c) return fail(TDSE_EINVAL, "NULL argument");
+    if (B < 1 || B > 65535) return fail(TDSE_EINVAL, "B must be in 1..65535");
+    if (!aligned16(c)) return fail(TDSE_EINVAL, "c must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = ctx->lmax + 1;
+    CUDA_TRY(ctx->part.ensure(sizeof(double) * 3 * (size_t)B * L));
+    CUDA_TRY(tdse::launch_pop_blocks((const double2 *)c, ctx->E.as<double>(), ctx->lmax, ctx->n, B, per_state, per_l,
+                                     ctx->part.as<double>(), s));
+    CUDA_TRY(tdse::launch_pop_totals(ctx->part.as<double>(), L, B, nullptr, bound, ionised, s));
+    return TDSE_OK;
+}
+
+tdse_status tdse_norm(tdse_ctx *ctx, const double *c, int B, double *out, void *stream)
+{
+    g_err.clear();
+    if (!ctx || !c || !out) return fail(TDSE_EINVAL, "NULL argument");
+    if (B < 1 || B > 65535) return fail(TDSE_EINVAL, "B must be in 1..65535");
+    if (!aligned16(c)) return fail(TDSE_EINVAL, "c must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = ctx->lmax + 1;
+    CUDA_TRY(ctx->part.ensure(sizeof(double) * 3 * (size_t)B * L));
+    CUDA_TRY(tdse::launch_pop_blocks((const double2 *)c, ctx->E.as<double>(), ctx->lmax, ctx->n, B, nullptr, nullptr,
+                                     ctx->part.as<double>(), s));
+    CUDA_TRY(tdse::launch_pop_totals(ctx->part.as<double>(), L, B, out, nullptr, nullptr, s));
+    return TDSE_OK;
+}
+
+tdse_status tdse_profile_enable(tdse_ctx *ctx, int on)
+{
+    g_err.clear();
+    if (!ctx) return fail(TDSE_EINVAL, "NULL context");
+    ctx->prof_on = on != 0;
+    return TDSE_OK;
+}
+
+tdse_status tdse_profile_read(tdse_ctx *ctx, double *mv_ms, long *mv_launches, long *kernel_launches)
+{
+    g_err.clear();
+    if (!ctx) return fail(TDSE_EINVAL, "NULL context");
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < ctx->prof_used; i += 2) {
+        CUDA_TRY(cudaEventSynchronize(ctx->prof_ev[i + 1]));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, ctx->prof_ev[i], ctx->prof_ev[i + 1]));
+        ms += t;
+    }
+    if (mv_ms) *mv_ms = ms;
+    if (mv_launches) *mv_launches = (long)(ctx->prof_used / 2);
+    if (kernel_launches) *kernel_launches = ctx->launches;
+    ctx->prof_used = 0;
+    ctx->launches = 0;
+    return TDSE_OK;
+}
+
+tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, int B, int samples_per_step,
+                                 double dt, long nsteps, tdse_scheme scheme, int taylor_order, int taylor_hold,
+                                 void *stream)
+{
+    (void)ctx; (void)c; (void)field; (void)B; (void)samples_per_step; (void)dt; (void)nsteps; (void)scheme;
+    (void)taylor_order; (void)taylor_hold; (void)stream;
+    return fail(TDSE_ENOTSUP, "tdse_propagate_batch is not available in this build yet");
+}
+
+tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, int samples_per_step, double dt,
+                         long nsteps, tdse_scheme scheme, int taylor_order, int taylor_hold, const double *weights,
+                         int checkpoint_every, double *grad_field, double *c_final, double *loss, void *stream)
+{
+    (void)ctx; (void)c0; (void)field; (void)samples_per_step; (void)dt; (void)nsteps; (void)scheme;
+    (void)taylor_order; (void)taylor_hold; (void)weights; (void)checkpoint_every; (void)grad_field; (void)c_final;
+    (void)loss; (void)stream;
+    return fail(TDSE_ENOTSUP, "tdse_adjoint is not available in this build yet");
+}
+
+struct tdse_group {
+    int dummy;
+};
+
+tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **out)
+{
+    (void)systems; (void)count;
+    if (out) *out = nullptr;
+    return fail(TDSE_ENOTSUP, "groups are not available in this build yet");
+}
+
+void tdse_group_destroy(tdse_group *g) { delete g; }
+
+tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const double *const *field_ptrs,
+                                 int samples_per_step, double dt, long nsteps, void *stream)
+{
+    (void)g; (void)c_ptrs; (void)field_ptrs; (void)samples_per_step; (void)dt; (void)nsteps; (void)stream;
+    return fail(TDSE_ENOTSUP, "groups are not available in this build yet");
+}
+
+}  // extern "C"

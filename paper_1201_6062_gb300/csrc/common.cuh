@@ -1,0 +1,203 @@
+// Device-side building blocks shared by the propagator kernels: complex
+// helpers, the three dipole-product precision policies and the data layout
+// descriptors.  sm_103a only.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tdse {
+
+// ---------------------------------------------------------------- layout --
+// One system (Hamiltonian + per-call state) as the kernels see it.
+//   U      dipole blocks in the storage format of the precision policy;
+//          block l starts at element l*bstride, row i at i*ld (ld >= n,
+//          ld % 4 == 0, padding columns are zero).
+//   E      FP64 energies [N].
+//   R      row sums  U_l x_{l+1}   [N] complex (rows of block l, l < lmax).
+//   P      column partials of U_l^T x_l, [nslots][n] complex; the slots of
+//          block l are sb[l] .. sb[l+1]-1 (one per row segment of U_l).
+//   c,x,acc  FP64 complex state vectors [N]: the solution, the stage input
+//          (or Taylor term) and the RK4 accumulator (or Taylor sum).
+//   xq     the next product's input in the policy's compute format.
+//   field  FP64 field samples.
+struct SysDesc {
+    const void *U;
+    long long bstride;
+    int ld, n, lmax, N;
+    const double *E;
+    double2 *R;
+    double2 *P;
+    const int *sb;
+    double2 *c, *x, *acc;
+    void *xq;
+    const double *field;
+};
+
+// A contiguous row range [i0, i1) of block l of system sys; its column
+// partial goes to slot `slot` of that system.
+struct Seg {
+    int sys, l, i0, i1, slot;
+};
+
+// ------------------------------------------------------------ precision --
+// Float-float value: hi + lo with |lo| <= ulp(hi)/2 after normalisation.
+struct df { float h, l; };
+
+__device__ __forceinline__ df df_two_sum(float a, float b)
+{
+    // Knuth's TwoSum: a + b = s + e exactly (round-to-nearest, no overflow).
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df{s, e};
+}
+
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    df s = df_two_sum(a.h, b.h);
+    float lo = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+    float h = __fadd_rn(s.h, lo);                      // Fast2Sum renormalisation
+    float l = __fsub_rn(lo, __fsub_rn(h, s.h));
+    return df{h, l};
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ df df_from_double(double v)
+{
+    float h = __double2float_rn(v);
+    float l = __double2float_rn(v - (double)h);
+    return df{h, l};
+}
+
+// a += (u.h + u.l) * (v.h + v.l), dropping u.l*v.l (relative 2^-48):
+// exact product u.h*v.h by TwoProd (one FMA), exact accumulation of its high
+// part by TwoSum, the low-order terms in plain FP32 into a.l.
+__device__ __forceinline__ void df_fma(df &a, df u, df v)
+{
+    float p = __fmul_rn(u.h, v.h);
+    float t = __fmaf_rn(u.h, v.h, -p);
+    t = __fmaf_rn(u.h, v.l, t);
+    t = __fmaf_rn(u.l, v.h, t);
+    df s = df_two_sum(a.h, p);
+    a.h = s.h;
+    a.l = __fadd_rn(a.l, __fadd_rn(s.l, t));
+}
+
+__device__ __forceinline__ double shfl_xor_d(double v, int m)
+{
+    return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+// FP64 products: U stored as double, 2 columns per 16-byte load.
+struct PolF64 {
+    static constexpr int CW = 2;
+    using Elem = double;
+    using Uv = double;
+    using Comp = double;
+    struct XV { double re, im; };
+    static __device__ __forceinline__ void load(const Elem *p, Uv u[CW])
+    {
+        double2 v = __ldcs(reinterpret_cast<const double2 *>(p));
+        u[0] = v.x; u[1] = v.y;
+    }
+    static __device__ __forceinline__ XV loadx(const void *xq, long long a)
+    {
+        double2 v = reinterpret_cast<const double2 *>(xq)[a];
+        return XV{v.x, v.y};
+    }
+    static __device__ __forceinline__ XV zerox() { return XV{0.0, 0.0}; }
+    static __device__ __forceinline__ Comp zero() { return 0.0; }
+    static __device__ __forceinline__ void fmax_(Comp &re, Comp &im, Uv u, const XV &x)
+    {
+        re = ::fma(u, x.re, re); im = ::fma(u, x.im, im);
+    }
+    static __device__ __forceinline__ Comp add(Comp a, Comp b) { return a + b; }
+    static __device__ __forceinline__ Comp shfl(Comp a, int m) { return shfl_xor_d(a, m); }
+    static __device__ __forceinline__ double to_double(Comp a) { return a; }
+    static __device__ __forceinline__ void store_xq(void *xq, long long a, double2 v)
+    {
+        reinterpret_cast<double2 *>(xq)[a] = v;
+    }
+};
+
+// FP32 products: U stored as float, 4 columns per 16-byte load.
+struct PolF32 {
+    static constexpr int CW = 4;
+    using Elem = float;
+    using Uv = float;
+    using Comp = float;
+    struct XV { float re, im; };
+    static __device__ __forceinline__ void load(const Elem *p, Uv u[CW])
+    {
+        float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+        u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
+    }
+    static __device__ __forceinline__ XV loadx(const void *xq, long long a)
+    {
+        float2 v = reinterpret_cast<const float2 *>(xq)[a];
+        return XV{v.x, v.y};
+    }
+    static __device__ __forceinline__ XV zerox() { return XV{0.f, 0.f}; }
+    static __device__ __forceinline__ Comp zero() { return 0.f; }
+    static __device__ __forceinline__ void fmax_(Comp &re, Comp &im, Uv u, const XV &x)
+    {
+        re = fmaf(u, x.re, re); im = fmaf(u, x.im, im);
+    }
+    static __device__ __forceinline__ Comp add(Comp a, Comp b) { return a + b; }
+    static __device__ __forceinline__ Comp shfl(Comp a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+    static __device__ __forceinline__ double to_double(Comp a) { return (double)a; }
+    static __device__ __forceinline__ void store_xq(void *xq, long long a, double2 v)
+    {
+        reinterpret_cast<float2 *>(xq)[a] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+    }
+};
+
+// Float-float products: U stored as (hi, lo) float pairs, 2 columns per
+// 16-byte load; x as (re.hi, re.lo, im.hi, im.lo).
+struct PolDF32 {
+    static constexpr int CW = 2;
+    using Elem = float2;
+    using Uv = df;
+    using Comp = df;
+    struct XV { df re, im; };
+    static __device__ __forceinline__ void load(const Elem *p, Uv u[CW])
+    {
+        float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+        u[0] = df{v.x, v.y}; u[1] = df{v.z, v.w};
+    }
+    static __device__ __forceinline__ XV loadx(const void *xq, long long a)
+    {
+        float4 v = reinterpret_cast<const float4 *>(xq)[a];
+        return XV{df{v.x, v.y}, df{v.z, v.w}};
+    }
+    static __device__ __forceinline__ XV zerox() { return XV{df{0.f, 0.f}, df{0.f, 0.f}}; }
+    static __device__ __forceinline__ Comp zero() { return df{0.f, 0.f}; }
+    static __device__ __forceinline__ void fmax_(Comp &re, Comp &im, Uv u, const XV &x)
+    {
+        df_fma(re, u, x.re); df_fma(im, u, x.im);
+    }
+    static __device__ __forceinline__ Comp add(Comp a, Comp b) { return df_add(a, b); }
+    static __device__ __forceinline__ Comp shfl(Comp a, int m)
+    {
+        return df{__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};
+    }
+    static __device__ __forceinline__ double to_double(Comp a) { return df_to_double(a); }
+    static __device__ __forceinline__ void store_xq(void *xq, long long a, double2 v)
+    {
+        df r = df_from_double(v.x), i = df_from_double(v.y);
+        reinterpret_cast<float4 *>(xq)[a] = make_float4(r.h, r.l, i.h, i.l);
+    }
+};
+
+// Field value at t_k + h*dt/2 (h = 0, 1, 2): step-grid samples take the mean
+// of the two neighbours at the half step; half-grid samples are read directly.
+__device__ __forceinline__ double field_at(const double *F, int sps, long long k, int h)
+{
+    if (sps == 2) return F[2 * k + h];
+    if (h == 0) return F[k];
+    if (h == 2) return F[k + 1];
+    return 0.5 * (F[k] + F[k + 1]);
+}
+
+}  // namespace tdse

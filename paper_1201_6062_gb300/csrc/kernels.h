@@ -1,0 +1,58 @@
+// Host-side launchers of the propagator kernels (implemented in the .cu
+// files of this directory).  Every launcher enqueues on `stream` and returns
+// the launch status; none synchronises.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace tdse {
+
+// Thread layout of the block mat-vec kernel for one (precision, n):
+// CT threads share one row (each owning MAXG groups of CW columns), RW rows
+// are processed at once, BT = CT*RW threads per CTA.
+struct MvCfg {
+    int idx;            // index into the instantiation table
+    int CT, RW, MAXG, BT;
+};
+
+// prec: 0 FP64, 1 FP32, 2 DF32 (tdse_precision values).
+bool mv_config(int prec, int n, MvCfg *out);
+int mv_ctas_per_sm(int prec, const MvCfg &cfg);
+
+// Block mat-vec over a segment list: R = U_l x_{l+1} rows, P = column partials.
+cudaError_t launch_mv(int prec, const MvCfg &cfg, int grid, const SysDesc *sys,
+                      const Seg *segs, const int *cta_off, cudaStream_t stream);
+
+// Epilogue modes.
+enum EpiMode { EPI_HX = 0, EPI_MIHX = 1, EPI_RK4 = 2, EPI_TAYLOR = 3 };
+
+// Per-amplitude epilogue over a block map (blk[b] = {sys, first amplitude}).
+//   EPI_HX / EPI_MIHX: y (= sys.acc) = H x or -i H x, f = fval.
+//   EPI_RK4:  stage `stage` (0..3) of step k.
+//   EPI_TAYLOR: term `stage` (1..K) of step k; hold selects the field time.
+struct EpiArgs {
+    int mode;
+    int stage;
+    int order;      // Taylor K
+    int hold;       // Taylor hold (0 left, 1 mid)
+    int sps;        // samples per step
+    long long k;    // step index
+    double dt;
+    double fval;    // field for EPI_HX / EPI_MIHX
+};
+cudaError_t launch_epi(int prec, int nblk, const int2 *blk, const SysDesc *sys,
+                       EpiArgs a, cudaStream_t stream);
+
+// xq = compute-format copy of c (the first product's input).
+cudaError_t launch_prep(int prec, int nblk, const int2 *blk, const SysDesc *sys,
+                        int from_x, cudaStream_t stream);
+
+// Populations: per (b, l): sum |c|^2, bound part, ionised part.
+//   part [B][L][3] scratch; then totals.
+cudaError_t launch_pop_blocks(const double2 *c, const double *E, int lmax, int n, int B,
+                              double *per_state, double *per_l, double *part,
+                              cudaStream_t stream);
+cudaError_t launch_pop_totals(const double *part, int L, int B, double *norm,
+                              double *bound, double *ionised, cudaStream_t stream);
+
+}  // namespace tdse

@@ -1,0 +1,196 @@
+"""ctypes binding of the C ABI in include/tdse.h (argument marshalling only).
+
+Every computation runs in the CUDA kernels of lib/libtdse.so; PyTorch only
+provides device memory and streams.  Importing this module loads the library
+and raises ImportError if it has not been built (there is no CPU fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libtdse.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libtdse.so is not built (run __graft_entry__.build() or python paper_1201_6062_gb300/build.py)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP = range(6)
+RK4, TAYLOR = 0, 1
+HOLD_LEFT, HOLD_MID = 0, 1
+FP64, FP32, DF32, BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "df32": DF32, "bf16x3": BF16X3}
+SCHEMES = {"rk4": RK4, "taylor": TAYLOR}
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_l = ctypes.c_long
+_d = ctypes.c_double
+
+_SIGS = {
+    "tdse_version": ([], _i),
+    "tdse_last_error": ([], ctypes.c_char_p),
+    "tdse_create": ([_vp, _vp, _i, _i, _i, ctypes.POINTER(_vp)], _i),
+    "tdse_destroy": ([_vp], None),
+    "tdse_size": ([_vp], _l),
+    "tdse_hmatvec": ([_vp, _d, _vp, _vp, _i, _vp], _i),
+    "tdse_propagate": ([_vp, _vp, _vp, _i, _d, _l, _i, _i, _i, _vp], _i),
+    "tdse_propagate_host": ([_vp, _vp, _vp, _i, _d, _l, _i, _i, _i, _vp], _i),
+    "tdse_norm": ([_vp, _vp, _i, _vp, _vp], _i),
+    "tdse_populations": ([_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "tdse_propagate_batch": ([_vp, _vp, _vp, _i, _i, _d, _l, _i, _i, _i, _vp], _i),
+    "tdse_adjoint": ([_vp, _vp, _vp, _i, _d, _l, _i, _i, _i, _vp, _i, _vp, _vp, _vp, _vp], _i),
+    "tdse_profile_enable": ([_vp, _i], _i),
+    "tdse_profile_read": ([_vp, ctypes.POINTER(_d), ctypes.POINTER(_l), ctypes.POINTER(_l)], _i),
+    "tdse_group_create": ([_vp, _i, ctypes.POINTER(_vp)], _i),
+    "tdse_group_destroy": ([_vp], None),
+    "tdse_group_propagate": ([_vp, _vp, _vp, _i, _d, _l, _vp], _i),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class TDSEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("tdse status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _check(st):
+    if st != OK:
+        raise TDSEError(st, _lib.tdse_last_error().decode())
+
+
+def version():
+    return _lib.tdse_version()
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_c(t, N, B=None, name="c"):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.complex128:
+        raise TypeError("%s must be a CUDA complex128 tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    want = N if B is None else B * N
+    if t.numel() != want:
+        raise ValueError("%s has %d amplitudes, expected %d" % (name, t.numel(), want))
+    return t
+
+
+def _dev_f64(t, n, name):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.float64:
+        raise TypeError("%s must be a CUDA float64 tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if n is not None and t.numel() != n:
+        raise ValueError("%s has %d samples, expected %d" % (name, t.numel(), n))
+    return t
+
+
+class Hamiltonian:
+    """One field-free Hamiltonian (energies E, upper dipole blocks U_l)
+    resident on the GPU in the storage format of `precision`."""
+
+    def __init__(self, energies, dipoles, lmax, n, precision="fp64"):
+        E = np.ascontiguousarray(energies, dtype=np.float64).reshape(-1)
+        if E.size != (lmax + 1) * n:
+            raise ValueError("energies must have (lmax+1)*n entries")
+        if lmax > 0:
+            U = np.ascontiguousarray(dipoles, dtype=np.float64).reshape(lmax, n, n)
+            up = U.ctypes.data_as(_vp)
+        else:
+            U, up = None, None
+        self.lmax, self.n, self.N = int(lmax), int(n), (lmax + 1) * n
+        self.precision = precision
+        h = _vp()
+        _check(_lib.tdse_create(E.ctypes.data_as(_vp), up, int(lmax), int(n), PRECISIONS[precision], ctypes.byref(h)))
+        self._h = h
+        self.energies = E
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tdse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def nfield(self, nsteps, samples_per_step=1):
+        return samples_per_step * nsteps + 1
+
+    def hmatvec(self, x, f, minus_i=False, y=None, stream=None):
+        x = _dev_c(x, self.N, name="x")
+        if y is None:
+            y = torch.empty_like(x)
+        _check(_lib.tdse_hmatvec(self._h, float(f), _ptr(x), _ptr(y), int(bool(minus_i)), _stream(stream)))
+        return y
+
+    def propagate(self, c, field, dt, nsteps, scheme="rk4", order=4, hold=HOLD_LEFT, samples_per_step=1,
+                  stream=None):
+        """Advance c (in place) over nsteps steps; returns c."""
+        c = _dev_c(c, self.N)
+        field = _dev_f64(field, self.nfield(nsteps, samples_per_step), "field")
+        _check(_lib.tdse_propagate(self._h, _ptr(c), _ptr(field), int(samples_per_step), float(dt), int(nsteps),
+                                   SCHEMES[scheme], int(order), int(hold), _stream(stream)))
+        return c
+
+    def propagate_host(self, c, field, dt, nsteps, scheme="rk4", order=4, hold=HOLD_LEFT, samples_per_step=1,
+                       stream=None):
+        """Same as propagate on host (CPU) tensors: copies in, propagates, copies back, synchronises."""
+        if c.device.type != "cpu" or c.dtype != torch.complex128 or not c.is_contiguous() or c.numel() != self.N:
+            raise TypeError("c must be a contiguous CPU complex128 tensor of N amplitudes")
+        if field.device.type != "cpu" or field.dtype != torch.float64 or not field.is_contiguous():
+            raise TypeError("field must be a contiguous CPU float64 tensor")
+        if field.numel() != self.nfield(nsteps, samples_per_step):
+            raise ValueError("field has the wrong number of samples")
+        _check(_lib.tdse_propagate_host(self._h, _ptr(c), _ptr(field), int(samples_per_step), float(dt), int(nsteps),
+                                        SCHEMES[scheme], int(order), int(hold), _stream(stream)))
+        return c
+
+    def norm(self, c, B=1, stream=None):
+        c = _dev_c(c, self.N, B)
+        out = torch.empty(B, dtype=torch.float64, device=c.device)
+        _check(_lib.tdse_norm(self._h, _ptr(c), int(B), _ptr(out), _stream(stream)))
+        return out
+
+    def populations(self, c, B=1, per_state=True, per_l=True, stream=None):
+        c = _dev_c(c, self.N, B)
+        dev = c.device
+        ps = torch.empty(B, self.N, dtype=torch.float64, device=dev) if per_state else None
+        pl = torch.empty(B, self.lmax + 1, dtype=torch.float64, device=dev) if per_l else None
+        bound = torch.empty(B, dtype=torch.float64, device=dev)
+        ion = torch.empty(B, dtype=torch.float64, device=dev)
+        _check(_lib.tdse_populations(self._h, _ptr(c), int(B), _ptr(ps), _ptr(pl), _ptr(bound), _ptr(ion),
+                                     _stream(stream)))
+        return dict(per_state=ps, per_l=pl, bound=bound, ionised=ion)
+
+    def profile(self, on=True):
+        """Enable or disable tracing of the block-product launches."""
+        _check(_lib.tdse_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self):
+        """(device ms of traced block products, their launches, all kernel launches) since the last read."""
+        ms, nmv, nk = _d(), _l(), _l()
+        _check(_lib.tdse_profile_read(self._h, ctypes.byref(ms), ctypes.byref(nmv), ctypes.byref(nk)))
+        return ms.value, nmv.value, nk.value

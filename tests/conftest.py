@@ -25,3 +25,12 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def tdse_lib():
+    """Builds (if needed) and imports the GPU binding."""
+    from paper_1201_6062_gb300 import build
+    build.build()
+    from paper_1201_6062_gb300 import tdse
+    return tdse
