@@ -150,6 +150,16 @@ tdse_status tdse_propagate_host(tdse_ctx *ctx, double *c_host, const double *fie
                                 void *stream);
 
 /*
+ * tdse_sync — waits for the work enqueued on `stream` and reports device-side
+ * failures of this context's kernels since the last check: TDSE_ETIMEOUT if a
+ * bounded wait inside a kernel gave up (every such wait stops after 2 s; the
+ * kernel then finishes without further waiting, and the results of the calls
+ * since the last check are invalid).  Clears the device status word.
+ * Errors: EINVAL, ECUDA, ETIMEOUT.
+ */
+tdse_status tdse_sync(tdse_ctx *ctx, void *stream);
+
+/*
  * tdse_norm — out[b] = sum_a |c[b][a]|^2 for b < B, FP64 with a fixed
  * reduction order (bitwise reproducible).  Unitarity is the error measure of
  * paper Sec. 5.1.

@@ -62,6 +62,7 @@ struct tdse_ctx {
     long long bstride = 0;
     DevBuf U, E, R, P, x, acc, xq, sb, sys;
     DevBuf part;                       // populations scratch
+    DevBuf errw;                       // device status word (kErrTimeout, ...)
     DevBuf hc, hfield;                 // device copies for the host-buffer entry point
     MvPlan plan;
     SysDesc desc{};                    // host copy of the descriptor (static fields filled)
@@ -103,8 +104,14 @@ static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std:
         nmax = n[s] > nmax ? n[s] : nmax;
         rows += (long long)lmax[s] * n[s];
     }
-    if (!tdse::mv_config(prec, nmax, &mp.cfg)) return fail(TDSE_ENOTSUP, "n=%d exceeds the supported maximum", nmax);
-    int G = sm_count() * tdse::mv_ctas_per_sm(prec, mp.cfg);
+    const int ldmax = (nmax + 3) & ~3;
+    int G;
+    if (tdse::mvt_config(prec, nmax, ldmax, &mp.cfg)) {
+        G = sm_count();                         // one ring CTA per SM (shared memory bound)
+    } else {
+        if (!tdse::mv_config(prec, nmax, &mp.cfg)) return fail(TDSE_ENOTSUP, "n=%d exceeds the supported maximum", nmax);
+        G = sm_count() * tdse::mv_ctas_per_sm(prec, mp.cfg);
+    }
     if (rows < G) G = (int)(rows > 0 ? rows : 1);
     tdse::make_plan(G, lmax, n, 32, plan);
     mp.grid = rows > 0 ? G : 0;
@@ -207,6 +214,8 @@ tdse_status tdse_create(const double *energies, const double *dipole_blocks, int
     CTRY(c->sb.ensure(sizeof(int) * (lmax + 1)));
     CTRY(cudaMemcpy(c->sb.p, plan.sb[0].data(), sizeof(int) * (lmax + 1), cudaMemcpyHostToDevice));
     CTRY(c->sys.ensure(sizeof(SysDesc)));
+    CTRY(c->errw.ensure(sizeof(int)));
+    CTRY(cudaMemset(c->errw.p, 0, sizeof(int)));
     CTRY(cudaMallocHost((void **)&c->stage, sizeof(SysDesc)));
     CTRY(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
 #undef CTRY
@@ -256,8 +265,12 @@ static tdse_status mv_and_epi(tdse_ctx *c, tdse::EpiArgs a, cudaStream_t s)
         if (st != TDSE_OK) return st;
         CUDA_TRY(cudaEventRecord(e0, s));
     }
-    CUDA_TRY(tdse::launch_mv(c->prec, c->plan.cfg, c->plan.grid, c->sys.as<SysDesc>(), c->plan.segs.as<Seg>(),
-                             c->plan.cta_off.as<int>(), s));
+    if (c->plan.cfg.tma)
+        CUDA_TRY(tdse::launch_mvt(c->prec, c->plan.cfg, c->plan.grid, c->sys.as<SysDesc>(), c->plan.segs.as<Seg>(),
+                                  c->plan.cta_off.as<int>(), c->errw.as<int>(), s));
+    else
+        CUDA_TRY(tdse::launch_mv(c->prec, c->plan.cfg, c->plan.grid, c->sys.as<SysDesc>(), c->plan.segs.as<Seg>(),
+                                 c->plan.cta_off.as<int>(), s));
     if (traced) CUDA_TRY(cudaEventRecord(e1, s));
     CUDA_TRY(tdse::launch_epi(c->prec, c->plan.nblk, c->plan.blk.as<int2>(), c->sys.as<SysDesc>(), a, s));
     c->launches += (c->plan.grid > 0 ? 1 : 0) + (c->plan.nblk > 0 ? 1 : 0);
@@ -368,7 +381,21 @@ tdse_status tdse_propagate_host(tdse_ctx *ctx, double *c_host, const double *fie
                         taylor_order, taylor_hold, s);
     if (st != TDSE_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(c_host, ctx->hc.p, cb, cudaMemcpyDeviceToHost, s));
+    return tdse_sync(ctx, stream);
+}
+
+tdse_status tdse_sync(tdse_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(TDSE_EINVAL, "NULL context");
+    cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaStreamSynchronize(s));
+    int w = 0;
+    CUDA_TRY(cudaMemcpy(&w, ctx->errw.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (w) {
+        CUDA_TRY(cudaMemset(ctx->errw.p, 0, sizeof(int)));
+        return fail(TDSE_ETIMEOUT, "a bounded device-side wait gave up (status word 0x%x); the results of the "
+                                   "calls since the last check are invalid", w);
+    }
     return TDSE_OK;
 }
 

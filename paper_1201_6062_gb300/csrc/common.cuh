@@ -18,7 +18,8 @@ namespace tdse {
 //          block l are sb[l] .. sb[l+1]-1 (one per row segment of U_l).
 //   c,x,acc  FP64 complex state vectors [N]: the solution, the stage input
 //          (or Taylor term) and the RK4 accumulator (or Taylor sum).
-//   xq     the next product's input in the policy's compute format.
+//   xq     the next product's input in the policy's compute format, 16 bytes
+//          per amplitude in every format.
 //   field  FP64 field samples.
 struct SysDesc {
     const void *U;
@@ -61,6 +62,14 @@ __device__ __forceinline__ df df_add(df a, df b)
     return df{h, l};
 }
 
+// a + b without the final renormalisation: the high parts are added exactly
+// (TwoSum) and all low-order terms are summed into the low word.
+__device__ __forceinline__ df df_add_lazy(df a, df b)
+{
+    df s = df_two_sum(a.h, b.h);
+    return df{s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
+}
+
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
 
 __device__ __forceinline__ df df_from_double(double v)
@@ -101,6 +110,11 @@ struct PolF64 {
         double2 v = __ldcs(reinterpret_cast<const double2 *>(p));
         u[0] = v.x; u[1] = v.y;
     }
+    static __device__ __forceinline__ void loads(const Elem *p, Uv u[CW])   // from shared memory
+    {
+        double2 v = *reinterpret_cast<const double2 *>(p);
+        u[0] = v.x; u[1] = v.y;
+    }
     static __device__ __forceinline__ XV loadx(const void *xq, long long a)
     {
         double2 v = reinterpret_cast<const double2 *>(xq)[a];
@@ -113,6 +127,7 @@ struct PolF64 {
         re = ::fma(u, x.re, re); im = ::fma(u, x.im, im);
     }
     static __device__ __forceinline__ Comp add(Comp a, Comp b) { return a + b; }
+    static __device__ __forceinline__ Comp add_fast(Comp a, Comp b) { return a + b; }
     static __device__ __forceinline__ Comp shfl(Comp a, int m) { return shfl_xor_d(a, m); }
     static __device__ __forceinline__ double to_double(Comp a) { return a; }
     static __device__ __forceinline__ void store_xq(void *xq, long long a, double2 v)
@@ -133,9 +148,15 @@ struct PolF32 {
         float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
         u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
     }
+    static __device__ __forceinline__ void loads(const Elem *p, Uv u[CW])   // from shared memory
+    {
+        float4 v = *reinterpret_cast<const float4 *>(p);
+        u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
+    }
+    // x is stored as (re, im, 0, 0) so that every format has 16-byte elements.
     static __device__ __forceinline__ XV loadx(const void *xq, long long a)
     {
-        float2 v = reinterpret_cast<const float2 *>(xq)[a];
+        float4 v = reinterpret_cast<const float4 *>(xq)[a];
         return XV{v.x, v.y};
     }
     static __device__ __forceinline__ XV zerox() { return XV{0.f, 0.f}; }
@@ -145,11 +166,12 @@ struct PolF32 {
         re = fmaf(u, x.re, re); im = fmaf(u, x.im, im);
     }
     static __device__ __forceinline__ Comp add(Comp a, Comp b) { return a + b; }
+    static __device__ __forceinline__ Comp add_fast(Comp a, Comp b) { return a + b; }
     static __device__ __forceinline__ Comp shfl(Comp a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
     static __device__ __forceinline__ double to_double(Comp a) { return (double)a; }
     static __device__ __forceinline__ void store_xq(void *xq, long long a, double2 v)
     {
-        reinterpret_cast<float2 *>(xq)[a] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+        reinterpret_cast<float4 *>(xq)[a] = make_float4(__double2float_rn(v.x), __double2float_rn(v.y), 0.f, 0.f);
     }
 };
 
@@ -166,6 +188,11 @@ struct PolDF32 {
         float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
         u[0] = df{v.x, v.y}; u[1] = df{v.z, v.w};
     }
+    static __device__ __forceinline__ void loads(const Elem *p, Uv u[CW])   // from shared memory
+    {
+        float4 v = *reinterpret_cast<const float4 *>(p);
+        u[0] = df{v.x, v.y}; u[1] = df{v.z, v.w};
+    }
     static __device__ __forceinline__ XV loadx(const void *xq, long long a)
     {
         float4 v = reinterpret_cast<const float4 *>(xq)[a];
@@ -178,6 +205,7 @@ struct PolDF32 {
         df_fma(re, u, x.re); df_fma(im, u, x.im);
     }
     static __device__ __forceinline__ Comp add(Comp a, Comp b) { return df_add(a, b); }
+    static __device__ __forceinline__ Comp add_fast(Comp a, Comp b) { return df_add_lazy(a, b); }
     static __device__ __forceinline__ Comp shfl(Comp a, int m)
     {
         return df{__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};

@@ -13,11 +13,19 @@ namespace tdse {
 struct MvCfg {
     int idx;            // index into the instantiation table
     int CT, RW, MAXG, BT;
+    int tma = 0;        // 1: bulk-copy ring kernel (mvt.cu), 0: per-thread loads (mv.cu)
+    int RS = 0;         // rows per ring stage (tma only)
 };
 
 // prec: 0 FP64, 1 FP32, 2 DF32 (tdse_precision values).
 bool mv_config(int prec, int n, MvCfg *out);
 int mv_ctas_per_sm(int prec, const MvCfg &cfg);
+
+// Ring-fed variant for rows of more than 128 column groups; false if n/ld do
+// not qualify.
+bool mvt_config(int prec, int n, int ld, MvCfg *out);
+cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys, const Seg *segs,
+                       const int *cta_off, int *err, cudaStream_t stream);
 
 // Block mat-vec over a segment list: R = U_l x_{l+1} rows, P = column partials.
 cudaError_t launch_mv(int prec, const MvCfg &cfg, int grid, const SysDesc *sys,

@@ -40,6 +40,7 @@ _SIGS = {
     "tdse_propagate": ([_vp, _vp, _vp, _i, _d, _l, _i, _i, _i, _vp], _i),
     "tdse_propagate_host": ([_vp, _vp, _vp, _i, _d, _l, _i, _i, _i, _vp], _i),
     "tdse_norm": ([_vp, _vp, _i, _vp, _vp], _i),
+    "tdse_sync": ([_vp, _vp], _i),
     "tdse_populations": ([_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "tdse_propagate_batch": ([_vp, _vp, _vp, _i, _i, _d, _l, _i, _i, _i, _vp], _i),
     "tdse_adjoint": ([_vp, _vp, _vp, _i, _d, _l, _i, _i, _i, _vp, _i, _vp, _vp, _vp, _vp], _i),
@@ -167,6 +168,10 @@ class Hamiltonian:
         _check(_lib.tdse_propagate_host(self._h, _ptr(c), _ptr(field), int(samples_per_step), float(dt), int(nsteps),
                                         SCHEMES[scheme], int(order), int(hold), _stream(stream)))
         return c
+
+    def sync(self, stream=None):
+        """Wait for this context's work and raise TDSEError on a device-side timeout."""
+        _check(_lib.tdse_sync(self._h, _stream(stream)))
 
     def norm(self, c, B=1, stream=None):
         c = _dev_c(c, self.N, B)

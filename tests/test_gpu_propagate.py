@@ -75,6 +75,21 @@ def test_hamiltonian_product_and_minus_i(tdse_lib, prec):
     assert rel(ym, -1j * ref) < tol
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_stale_shared_memory_does_not_leak(tdse_lib, prec):
+    """A product on NaN input leaves NaN in the kernels' shared-memory staging;
+    the next products (segments ending inside a stage) must not pick it up."""
+    for lmax, n in ((1, 300), (2, 1000), (3, 517), (2, 2000)):
+        _, U = system(lmax, n, 5)
+        H = tdse_lib.Hamiltonian(np.zeros((lmax + 1) * n), U, lmax, n, prec)
+        bad = torch.full(((lmax + 1) * n,), float("nan"), dtype=torch.complex128, device="cuda")
+        H.hmatvec(bad, 1.0)
+        x = inputs.random_state((lmax + 1) * n, 6)
+        y = H.hmatvec(to_dev(x), 1.0).cpu().numpy()
+        assert np.all(np.isfinite(y)), (lmax, n)
+        assert rel(y, oracle.dmatvec(lmax, n, U, x)) < DX_TOL[prec]
+
+
 def test_product_is_bitwise_reproducible(tdse_lib):
     lmax, n = 6, 700
     E, U = system(lmax, n, 9)
@@ -175,9 +190,11 @@ def test_bad_arguments_raise(tdse_lib):
     with pytest.raises(ValueError):
         H.propagate(c, dev_f64(np.zeros(3)), 0.1, 5)
     with pytest.raises(tdse_lib.TDSEError):
-        H.propagate(c, dev_f64(np.zeros(11)), 0.1, 5, "taylor", order=0)
+        H.propagate(c, dev_f64(np.zeros(6)), 0.1, 5, "taylor", order=0)
     with pytest.raises(tdse_lib.TDSEError):
-        H.propagate(c, dev_f64(np.zeros(11)), float("nan"), 5)
+        H.propagate(c, dev_f64(np.zeros(6)), float("nan"), 5)
+    with pytest.raises(tdse_lib.TDSEError):
+        H.propagate(c, dev_f64(np.zeros(16)), 0.1, 5, samples_per_step=3)
 
 
 # ----------------------------------------------------------- populations --
