@@ -230,6 +230,30 @@ tdse_status tdse_profile_enable(tdse_ctx *ctx, int on);
 tdse_status tdse_profile_read(tdse_ctx *ctx, double *mv_ms, long *mv_launches, long *kernel_launches);
 
 /*
+ * tdse_populations_noalloc — the populations of tdse_populations for callers
+ * that cannot allocate device memory when they need them (for example when
+ * another framework's allocator already holds all device memory, or inside a
+ * latency-critical loop where an allocation would synchronise the device).
+ * It needs no context and calls no allocator; the paper has no counterpart
+ * (it is a deployment convenience of this library).
+ *   c          device, complex [B][N], N = (lmax+1)*n, 16-byte aligned.
+ *   energies   device, FP64 [N] (decides bound E < 0 vs ionised E >= 0).
+ *   per_state, per_l, bound, ionised: device outputs as in tdse_populations,
+ *              any may be NULL.
+ * Limit: B*(lmax+1) <= 16384; larger requests fail with TDSE_EINVAL.
+ * Scratch: one fixed 384 KB device array per GPU, held until the process
+ * exits and shared by every call; each call writes every entry it later
+ * reads, but calls whose kernels overlap on the GPU (different streams, no
+ * ordering between them) race on it and must be serialised by the caller.
+ * The first call on each device resolves the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Asynchronous on `stream`.  Errors: EINVAL, ECUDA.
+ */
+tdse_status tdse_populations_noalloc(const double *c, const double *energies, int lmax, int n, int B,
+                                     double *per_state, double *per_l, double *bound, double *ionised,
+                                     void *stream);
+
+/*
  * Uneven batches: several contexts of different (lmax, n) advanced together,
  * one kernel launch per stage for all of them (rows of every system are split
  * evenly over the GPU's SMs).  All contexts must share one precision.

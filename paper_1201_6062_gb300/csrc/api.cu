@@ -27,6 +27,15 @@ static tdse_status fail(tdse_status s, const char *fmt, ...)
     return s;
 }
 
+namespace tdse {
+// Records a failure for tdse_last_error() from the library's other translation units.
+tdse_status set_error(tdse_status s, const char *msg)
+{
+    g_err = msg;
+    return s;
+}
+}  // namespace tdse
+
 #define CUDA_TRY(call)                                                                           \
     do {                                                                                         \
         cudaError_t e_ = (call);                                                                 \
