@@ -1,0 +1,172 @@
+// Discrete adjoint of the RK4 and Taylor propagators (discretise, then
+// differentiate; the paper has no adjoint).
+//
+// For a step c' = Phi(c; f) built from products k = M(f) x with
+// M(f) = -i (diag(E) + f D) and D real symmetric, the cotangents run
+// backwards through the same products with M^dagger = +i H:
+//   g_x = i (E g_k + f D g_k),   dL/df += Re<g_k, -i D x> = Im<D g_k, x>.
+// D g_k comes from the same block mat-vec kernels as the forward pass (its
+// input is the cotangent g_k); this file holds the per-amplitude epilogue of
+// one reverse stage, the loss initialisation and the ordered flush that adds
+// each stage's field-gradient contribution.  All FP64; sums in fixed order.
+#include "kernels.h"
+
+namespace tdse {
+
+// Sum of v over a 256-thread block in fixed order, valid in thread 0.
+__device__ __forceinline__ double block_sum_fixed(double v, double *sh)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 8; ++q) s += sh[q];
+    return s;
+}
+
+__device__ __forceinline__ void do_flush(const Flush &f)
+{
+    if (!f.parts) return;
+    double s = 0.0;
+    for (int q = 0; q < f.n; ++q) s += f.parts[q];
+    if (f.i0 >= 0) f.target[f.i0] += f.w0 * s;
+    if (f.i1 >= 0) f.target[f.i1] += f.w1 * s;
+}
+
+template <class P>
+__global__ void __launch_bounds__(256)
+adj_epi_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, AdjArgs A)
+{
+    __shared__ double sh[8];
+    if (blockIdx.x == 0 && threadIdx.x == 0) do_flush(A.flush);
+    const int2 bm = blk[blockIdx.x];
+    const SysDesc &S = sys[bm.x];
+    const long long a = (long long)bm.y + threadIdx.x;
+    double dot = 0.0;
+    if (a < S.N) {
+        const int n = S.n;
+        const int m = (int)(a / n), i = (int)(a - (long long)m * n);
+        // u = D g
+        double ur = 0.0, ui = 0.0;
+        if (m < S.lmax) { const double2 r = S.R[a]; ur = r.x; ui = r.y; }
+        if (m >= 1) {
+            const int b0 = S.sb[m - 1], b1 = S.sb[m];
+            for (int s = b0; s < b1; ++s) { const double2 p = S.P[(long long)s * n + i]; ur += p.x; ui += p.y; }
+        }
+        const double2 g = S.x[a];
+        const double e = S.E[a];
+        double f;
+        if (A.scheme == 0) {
+            const int h = (A.stage == 0) ? 0 : (A.stage == 3 ? 2 : 1);
+            f = field_at(S.field, A.sps, A.k, h);
+        } else {
+            f = field_at(S.field, A.sps, A.k, A.hold ? 1 : 0);
+        }
+        // g_x = i (E g + f u) = i (p + i q) = (-q, p)
+        const double p = e * g.x + f * ur;
+        const double q = e * g.y + f * ui;
+        const double gxr = -q, gxi = p;
+        const double2 xs = A.fwd[a];
+        dot = ur * xs.y - ui * xs.x;             // Im(conj(u) x)
+        const double2 G = A.G[a];
+        const double dt = A.dt;
+        double2 next;
+        if (A.scheme == 0) {
+            if (A.stage == 3) {
+                S.acc[a] = make_double2(G.x + gxr, G.y + gxi);
+                next = make_double2(dt / 3.0 * G.x + dt * gxr, dt / 3.0 * G.y + dt * gxi);
+            } else if (A.stage == 2) {
+                const double2 gc = S.acc[a];
+                S.acc[a] = make_double2(gc.x + gxr, gc.y + gxi);
+                next = make_double2(dt / 3.0 * G.x + 0.5 * dt * gxr, dt / 3.0 * G.y + 0.5 * dt * gxi);
+            } else if (A.stage == 1) {
+                const double2 gc = S.acc[a];
+                S.acc[a] = make_double2(gc.x + gxr, gc.y + gxi);
+                next = make_double2(dt / 6.0 * G.x + 0.5 * dt * gxr, dt / 6.0 * G.y + 0.5 * dt * gxi);
+            } else {
+                const double2 gc = S.acc[a];
+                const double2 Gn = make_double2(gc.x + gxr, gc.y + gxi);   // dL/dc_k
+                A.G[a] = Gn;
+                next = make_double2(dt / 6.0 * Gn.x, dt / 6.0 * Gn.y);     // input of step k-1, stage 3
+            }
+        } else {
+            // term m: Gamma_{m-1} = G + g_x; next input (dt/(m-1)) Gamma_{m-1},
+            // or at m = 1 the new G and the previous step's (dt/K) G.
+            const double2 Gm = make_double2(G.x + gxr, G.y + gxi);
+            if (A.stage > 1) {
+                const double s = dt / (double)(A.stage - 1);
+                next = make_double2(s * Gm.x, s * Gm.y);
+            } else {
+                A.G[a] = Gm;
+                const double s = dt / (double)A.order;
+                next = make_double2(s * Gm.x, s * Gm.y);
+            }
+        }
+        S.x[a] = next;
+        P::store_xq(S.xq, a, next);
+    }
+    const double tot = block_sum_fixed(dot, sh);
+    if (threadIdx.x == 0) A.dots[blockIdx.x] = tot;
+}
+
+template <class P>
+__global__ void __launch_bounds__(256)
+adj_init_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, const double2 *__restrict__ cT,
+                const double *__restrict__ w, double2 *__restrict__ G, double scale, double *__restrict__ parts)
+{
+    __shared__ double sh[8];
+    const int2 bm = blk[blockIdx.x];
+    const SysDesc &S = sys[bm.x];
+    const long long a = (long long)bm.y + threadIdx.x;
+    double l = 0.0;
+    if (a < S.N) {
+        const double2 c = cT[a];
+        const double wa = w[a];
+        l = wa * (c.x * c.x + c.y * c.y);
+        const double2 g = make_double2(2.0 * wa * c.x, 2.0 * wa * c.y);
+        G[a] = g;
+        const double2 next = make_double2(scale * g.x, scale * g.y);
+        S.x[a] = next;
+        P::store_xq(S.xq, a, next);
+    }
+    const double tot = block_sum_fixed(l, sh);
+    if (threadIdx.x == 0) parts[blockIdx.x] = tot;
+}
+
+__global__ void flush_kernel(Flush f) { do_flush(f); }
+
+cudaError_t launch_adj_epi(int prec, int nblk, const int2 *blk, const SysDesc *sys, AdjArgs a, cudaStream_t stream)
+{
+    if (nblk <= 0) return cudaSuccess;
+    switch (prec) {
+    case 0: adj_epi_kernel<PolF64><<<nblk, 256, 0, stream>>>(sys, blk, a); break;
+    case 1: adj_epi_kernel<PolF32><<<nblk, 256, 0, stream>>>(sys, blk, a); break;
+    case 2: adj_epi_kernel<PolDF32><<<nblk, 256, 0, stream>>>(sys, blk, a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(int prec, int nblk, const int2 *blk, const SysDesc *sys, const double2 *c, const double *w,
+                            double2 *G, double scale, double *parts, cudaStream_t stream)
+{
+    if (nblk <= 0) return cudaSuccess;
+    switch (prec) {
+    case 0: adj_init_kernel<PolF64><<<nblk, 256, 0, stream>>>(sys, blk, c, w, G, scale, parts); break;
+    case 1: adj_init_kernel<PolF32><<<nblk, 256, 0, stream>>>(sys, blk, c, w, G, scale, parts); break;
+    case 2: adj_init_kernel<PolDF32><<<nblk, 256, 0, stream>>>(sys, blk, c, w, G, scale, parts); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flush(Flush f, cudaStream_t stream)
+{
+    flush_kernel<<<1, 1, 0, stream>>>(f);
+    return cudaGetLastError();
+}
+
+}  // namespace tdse

@@ -73,9 +73,11 @@ struct tdse_ctx {
     DevBuf part;                       // populations scratch
     DevBuf errw;                       // device status word (kErrTimeout, ...)
     DevBuf hc, hfield;                 // device copies for the host-buffer entry point
+    // adjoint: working state, checkpoints, stage store, cotangents, partial sums
+    DevBuf ac, ckpt, store, aG, ag, agc, axq, dots, lparts;
     MvPlan plan;
     SysDesc desc{};                    // host copy of the descriptor (static fields filled)
-    SysDesc *stage = nullptr;          // pinned staging for descriptor uploads
+    SysDesc *stage = nullptr;          // pinned staging for descriptor uploads (2 slots)
     cudaEvent_t stage_ev = nullptr;
     bool stage_pending = false;
     int nslots = 0;
@@ -222,10 +224,10 @@ tdse_status tdse_create(const double *energies, const double *dipole_blocks, int
     CTRY(c->xq.ensure((size_t)16 * c->N));
     CTRY(c->sb.ensure(sizeof(int) * (lmax + 1)));
     CTRY(cudaMemcpy(c->sb.p, plan.sb[0].data(), sizeof(int) * (lmax + 1), cudaMemcpyHostToDevice));
-    CTRY(c->sys.ensure(sizeof(SysDesc)));
+    CTRY(c->sys.ensure(2 * sizeof(SysDesc)));
     CTRY(c->errw.ensure(sizeof(int)));
     CTRY(cudaMemset(c->errw.p, 0, sizeof(int)));
-    CTRY(cudaMallocHost((void **)&c->stage, sizeof(SysDesc)));
+    CTRY(cudaMallocHost((void **)&c->stage, 2 * sizeof(SysDesc)));
     CTRY(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
 #undef CTRY
     SysDesc &d = c->desc;
@@ -238,12 +240,14 @@ tdse_status tdse_create(const double *energies, const double *dipole_blocks, int
 
 void tdse_destroy(tdse_ctx *ctx) { delete ctx; }
 
-// Upload a descriptor through the pinned staging slot (stream ordered).
-static tdse_status stage_desc(tdse_ctx *c, const SysDesc &d, cudaStream_t s)
+// Upload one or two descriptors through the pinned staging slots (stream
+// ordered; the previous upload must have left the staging memory first).
+static tdse_status stage_desc(tdse_ctx *c, const SysDesc &d, cudaStream_t s, const SysDesc *d2 = nullptr)
 {
     if (c->stage_pending) CUDA_TRY(cudaEventSynchronize(c->stage_ev));
-    *c->stage = d;
-    CUDA_TRY(cudaMemcpyAsync(c->sys.p, c->stage, sizeof(SysDesc), cudaMemcpyHostToDevice, s));
+    c->stage[0] = d;
+    if (d2) c->stage[1] = *d2;
+    CUDA_TRY(cudaMemcpyAsync(c->sys.p, c->stage, (d2 ? 2 : 1) * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaEventRecord(c->stage_ev, s));
     c->stage_pending = true;
     return TDSE_OK;
@@ -265,24 +269,36 @@ static tdse_status prof_pair(tdse_ctx *c, cudaEvent_t *e0, cudaEvent_t *e1)
     return TDSE_OK;
 }
 
-static tdse_status mv_and_epi(tdse_ctx *c, tdse::EpiArgs a, cudaStream_t s)
+// The block mat-vec of descriptor slot `slot` (0 forward state, 1 adjoint
+// cotangents), traced when profiling is on.
+static tdse_status launch_product(tdse_ctx *c, int slot, cudaStream_t s)
 {
+    if (c->plan.grid <= 0) return TDSE_OK;
+    const SysDesc *sys = c->sys.as<SysDesc>() + slot;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    const bool traced = c->prof_on && c->plan.grid > 0;
+    const bool traced = c->prof_on;
     if (traced) {
         tdse_status st = prof_pair(c, &e0, &e1);
         if (st != TDSE_OK) return st;
         CUDA_TRY(cudaEventRecord(e0, s));
     }
     if (c->plan.cfg.tma)
-        CUDA_TRY(tdse::launch_mvt(c->prec, c->plan.cfg, c->plan.grid, c->sys.as<SysDesc>(), c->plan.segs.as<Seg>(),
+        CUDA_TRY(tdse::launch_mvt(c->prec, c->plan.cfg, c->plan.grid, sys, c->plan.segs.as<Seg>(),
                                   c->plan.cta_off.as<int>(), c->errw.as<int>(), s));
     else
-        CUDA_TRY(tdse::launch_mv(c->prec, c->plan.cfg, c->plan.grid, c->sys.as<SysDesc>(), c->plan.segs.as<Seg>(),
+        CUDA_TRY(tdse::launch_mv(c->prec, c->plan.cfg, c->plan.grid, sys, c->plan.segs.as<Seg>(),
                                  c->plan.cta_off.as<int>(), s));
     if (traced) CUDA_TRY(cudaEventRecord(e1, s));
+    c->launches += 1;
+    return TDSE_OK;
+}
+
+static tdse_status mv_and_epi(tdse_ctx *c, tdse::EpiArgs a, cudaStream_t s)
+{
+    tdse_status st = launch_product(c, 0, s);
+    if (st != TDSE_OK) return st;
     CUDA_TRY(tdse::launch_epi(c->prec, c->plan.nblk, c->plan.blk.as<int2>(), c->sys.as<SysDesc>(), a, s));
-    c->launches += (c->plan.grid > 0 ? 1 : 0) + (c->plan.nblk > 0 ? 1 : 0);
+    c->launches += (c->plan.nblk > 0 ? 1 : 0);
     return TDSE_OK;
 }
 
@@ -475,14 +491,155 @@ tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, 
     return fail(TDSE_ENOTSUP, "tdse_propagate_batch is not available in this build yet");
 }
 
+// Field samples that a stage's field value depends on, with weights
+// (reading of the field samples: linear mean at half steps on the step grid).
+static void field_deps(int sps, long k, int h, long long *i0, long long *i1, double *w0, double *w1)
+{
+    *i1 = -1;
+    *w1 = 0.0;
+    *w0 = 1.0;
+    if (sps == 2) { *i0 = 2 * (long long)k + h; return; }
+    if (h == 0) { *i0 = k; return; }
+    if (h == 2) { *i0 = k + 1; return; }
+    *i0 = k; *i1 = k + 1; *w0 = 0.5; *w1 = 0.5;
+}
+
 tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, int samples_per_step, double dt,
                          long nsteps, tdse_scheme scheme, int taylor_order, int taylor_hold, const double *weights,
                          int checkpoint_every, double *grad_field, double *c_final, double *loss, void *stream)
 {
-    (void)ctx; (void)c0; (void)field; (void)samples_per_step; (void)dt; (void)nsteps; (void)scheme;
-    (void)taylor_order; (void)taylor_hold; (void)weights; (void)checkpoint_every; (void)grad_field; (void)c_final;
-    (void)loss; (void)stream;
-    return fail(TDSE_ENOTSUP, "tdse_adjoint is not available in this build yet");
+    g_err.clear();
+    tdse_status st = check_prop_args(ctx, c0, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold);
+    if (st != TDSE_OK) return st;
+    if (!weights || !grad_field) return fail(TDSE_EINVAL, "weights and grad_field must not be NULL");
+    if (checkpoint_every < 1) return fail(TDSE_EINVAL, "checkpoint_every must be >= 1");
+    if (c_final && !aligned16(c_final)) return fail(TDSE_EINVAL, "c_final must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sps = samples_per_step;
+    const bool rk4 = scheme == TDSE_RK4;
+    const int order = rk4 ? 4 : taylor_order;
+    const int nst = rk4 ? 4 : taylor_order;            // stored stage inputs per step
+    const size_t vb = sizeof(double2) * (size_t)ctx->N;
+    const long K = checkpoint_every;
+    const long nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+    const long kseg = nsteps < K ? nsteps : K;
+    const int nblk = ctx->plan.nblk;
+    CUDA_TRY(ctx->ac.ensure(vb));
+    CUDA_TRY(ctx->ckpt.ensure(vb * (size_t)(nseg > 0 ? nseg : 1)));
+    CUDA_TRY(ctx->store.ensure(vb * (size_t)(kseg > 0 ? kseg : 1) * nst));
+    CUDA_TRY(ctx->aG.ensure(vb));
+    CUDA_TRY(ctx->ag.ensure(vb));
+    CUDA_TRY(ctx->agc.ensure(vb));
+    CUDA_TRY(ctx->axq.ensure((size_t)16 * ctx->N));
+    CUDA_TRY(ctx->dots.ensure(sizeof(double) * 2 * (size_t)(nblk > 0 ? nblk : 1)));
+    CUDA_TRY(ctx->lparts.ensure(sizeof(double) * (size_t)(nblk > 0 ? nblk : 1)));
+    const size_t nF = (size_t)sps * nsteps + 1;
+    CUDA_TRY(cudaMemsetAsync(grad_field, 0, sizeof(double) * nF, s));
+    if (loss) CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(double), s));
+
+    double2 *cw = ctx->ac.as<double2>();
+    auto ckpt = [&](long j) { return ctx->ckpt.as<double2>() + (size_t)j * ctx->N; };
+    auto store = [&](long i, int q) { return ctx->store.as<double2>() + ((size_t)i * nst + q) * ctx->N; };
+    SysDesc fwd = ctx->desc;
+    fwd.c = cw;
+    fwd.field = field;
+    SysDesc adj = ctx->desc;
+    adj.c = nullptr;
+    adj.x = ctx->ag.as<double2>();
+    adj.acc = ctx->agc.as<double2>();
+    adj.xq = ctx->axq.p;
+    adj.field = field;
+    st = stage_desc(ctx, fwd, s, &adj);
+    if (st != TDSE_OK) return st;
+    const SysDesc *dfwd = ctx->sys.as<SysDesc>();
+    const SysDesc *dadj = dfwd + 1;
+
+    // ---- forward pass, keeping c at the start of every segment
+    CUDA_TRY(cudaMemcpyAsync(cw, c0, vb, cudaMemcpyDeviceToDevice, s));
+    if (nseg > 0) CUDA_TRY(cudaMemcpyAsync(ckpt(0), c0, vb, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(tdse::launch_prep(ctx->prec, nblk, ctx->plan.blk.as<int2>(), dfwd, 0, s));
+    ctx->launches += 1;
+    tdse::EpiArgs a{};
+    a.sps = sps;
+    a.dt = dt;
+    a.order = order;
+    a.hold = taylor_hold;
+    a.mode = rk4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
+    for (long k = 0; k < nsteps; ++k) {
+        a.k = k;
+        const bool cp = ((k + 1) % K == 0) && (k + 1) < nsteps;
+        for (int q = rk4 ? 0 : 1; q <= (rk4 ? 3 : order); ++q) {
+            a.stage = q;
+            a.st_x = nullptr;
+            a.st_c = (cp && q == (rk4 ? 3 : order)) ? ckpt((k + 1) / K) : nullptr;
+            st = mv_and_epi(ctx, a, s);
+            if (st != TDSE_OK) return st;
+        }
+    }
+    if (c_final) CUDA_TRY(cudaMemcpyAsync(c_final, cw, vb, cudaMemcpyDeviceToDevice, s));
+
+    // ---- loss, dL/dc_N and the first reverse-stage input
+    const double scale = rk4 ? dt / 6.0 : dt / (double)order;
+    CUDA_TRY(tdse::launch_adj_init(ctx->prec, nblk, ctx->plan.blk.as<int2>(), dadj, cw, weights,
+                                   ctx->aG.as<double2>(), scale, ctx->lparts.as<double>(), s));
+    ctx->launches += 1;
+    tdse::Flush pending{};
+    if (loss) pending = tdse::Flush{ctx->lparts.as<double>(), nblk, loss, 0, -1, 1.0, 0.0};
+
+    // ---- backward over the segments, last first
+    long t = 0;
+    for (long j = nseg - 1; j >= 0; --j) {
+        const long k0 = j * K;
+        const long ns = (k0 + K <= nsteps) ? K : nsteps - k0;
+        // recompute the segment's stage inputs from its checkpoint
+        CUDA_TRY(cudaMemcpyAsync(cw, ckpt(j), vb, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(tdse::launch_prep(ctx->prec, nblk, ctx->plan.blk.as<int2>(), dfwd, 0, s));
+        ctx->launches += 1;
+        for (long i = 0; i < ns; ++i) {
+            a.k = k0 + i;
+            const int qlast = rk4 ? 3 : order;
+            for (int q = rk4 ? 0 : 1; q <= qlast; ++q) {
+                if (i == ns - 1 && q == qlast) break;       // c_{k0+ns} is not needed
+                a.stage = q;
+                a.st_x = (q < qlast) ? store(i, rk4 ? q + 1 : q) : nullptr;
+                a.st_c = (q == qlast) ? store(i + 1, 0) : nullptr;
+                st = mv_and_epi(ctx, a, s);
+                if (st != TDSE_OK) return st;
+            }
+        }
+        // reverse stages of the segment's steps
+        for (long i = ns - 1; i >= 0; --i) {
+            const long k = k0 + i;
+            for (int q = rk4 ? 3 : order; q >= (rk4 ? 0 : 1); --q) {
+                tdse::AdjArgs A{};
+                A.scheme = rk4 ? 0 : 1;
+                A.stage = q;
+                A.order = order;
+                A.hold = taylor_hold;
+                A.sps = sps;
+                A.k = k;
+                A.dt = dt;
+                const int fq = rk4 ? q : q - 1;                  // which stored stage input
+                A.fwd = (fq == 0 && i == 0) ? ckpt(j) : store(i, fq);
+                A.G = ctx->aG.as<double2>();
+                A.dots = ctx->dots.as<double>() + (size_t)(t & 1) * nblk;
+                A.flush = pending;
+                st = launch_product(ctx, 1, s);
+                if (st != TDSE_OK) return st;
+                CUDA_TRY(tdse::launch_adj_epi(ctx->prec, nblk, ctx->plan.blk.as<int2>(), dadj, A, s));
+                ctx->launches += 1;
+                const int h = rk4 ? ((q == 0) ? 0 : (q == 3 ? 2 : 1)) : (taylor_hold ? 1 : 0);
+                pending = tdse::Flush{A.dots, nblk, grad_field, 0, -1, 1.0, 0.0};
+                field_deps(sps, k, h, &pending.i0, &pending.i1, &pending.w0, &pending.w1);
+                ++t;
+            }
+        }
+    }
+    if (pending.parts) {
+        CUDA_TRY(tdse::launch_flush(pending, s));
+        ctx->launches += 1;
+    }
+    return TDSE_OK;
 }
 
 struct tdse_group {

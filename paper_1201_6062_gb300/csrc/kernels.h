@@ -47,9 +47,45 @@ struct EpiArgs {
     long long k;    // step index
     double dt;
     double fval;    // field for EPI_HX / EPI_MIHX
+    double2 *st_x;  // if set: also store this stage's new x (next stage input / Taylor term)
+    double2 *st_c;  // if set: also store the new c (last RK4 stage / last Taylor term)
 };
 cudaError_t launch_epi(int prec, int nblk, const int2 *blk, const SysDesc *sys,
                        EpiArgs a, cudaStream_t stream);
+
+// --- adjoint (adj.cu) ---
+// A pending scalar: the sum of parts[0..n) (fixed order) is added, times w0 and
+// w1, to target[i0] and target[i1] (an index < 0 is skipped).
+struct Flush {
+    const double *parts;
+    int n;
+    double *target;
+    long long i0, i1;
+    double w0, w1;
+};
+// Reverse stage of RK4 (stage 3..0) or Taylor term (order..1) of step k:
+// product input g in sys.x, D g in R/P, forward stage input in fwd, dL/dc_{k+1}
+// in G, running dL/dc_k in sys.acc; writes the next product input to sys.x/xq,
+// the block partials of Im<D g, fwd> to dots, and performs `flush` first.
+struct AdjArgs {
+    int scheme;      // 0 RK4, 1 Taylor
+    int stage;       // RK4: 3..0; Taylor: term m = order..1
+    int order;
+    int hold;
+    int sps;
+    long long k;
+    double dt;
+    const double2 *fwd;
+    double2 *G;
+    double *dots;
+    Flush flush;
+};
+cudaError_t launch_adj_epi(int prec, int nblk, const int2 *blk, const SysDesc *sys, AdjArgs a, cudaStream_t stream);
+// L = sum w |c|^2 (block partials into parts), G = 2 w c, first product input
+// g = scale * G into sys.x / xq.
+cudaError_t launch_adj_init(int prec, int nblk, const int2 *blk, const SysDesc *sys, const double2 *c, const double *w,
+                            double2 *G, double scale, double *parts, cudaStream_t stream);
+cudaError_t launch_flush(Flush f, cudaStream_t stream);
 
 // xq = compute-format copy of c (the first product's input).
 cudaError_t launch_prep(int prec, int nblk, const int2 *blk, const SysDesc *sys,

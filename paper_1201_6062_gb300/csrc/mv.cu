@@ -299,6 +299,7 @@ epi_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, EpiArg
             const double2 xn = make_double2(c.x + 0.5 * dt * kr, c.y + 0.5 * dt * ki);
             S.x[a] = xn;
             P::store_xq(S.xq, a, xn);
+            if (A.st_x) A.st_x[a] = xn;
         } else if (A.stage < 3) {
             const double2 ac = S.acc[a];
             S.acc[a] = make_double2(ac.x + 2.0 * kr, ac.y + 2.0 * ki);
@@ -306,12 +307,14 @@ epi_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, EpiArg
             const double2 xn = make_double2(c.x + s * kr, c.y + s * ki);
             S.x[a] = xn;
             P::store_xq(S.xq, a, xn);
+            if (A.st_x) A.st_x[a] = xn;
         } else {
             const double2 ac = S.acc[a];
             const double w = dt / 6.0;
             const double2 cn = make_double2(c.x + w * (ac.x + kr), c.y + w * (ac.y + ki));
             S.c[a] = cn;
             P::store_xq(S.xq, a, cn);
+            if (A.st_c) A.st_c[a] = cn;
         }
         return;
     }
@@ -329,9 +332,11 @@ epi_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, EpiArg
         S.acc[a] = sum;
         S.x[a] = T;
         P::store_xq(S.xq, a, T);
+        if (A.st_x) A.st_x[a] = T;
     } else {
         S.c[a] = sum;
         P::store_xq(S.xq, a, sum);
+        if (A.st_c) A.st_c[a] = sum;
     }
 }
 

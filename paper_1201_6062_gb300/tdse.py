@@ -199,3 +199,42 @@ class Hamiltonian:
         ms, nmv, nk = _d(), _l(), _l()
         _check(_lib.tdse_profile_read(self._h, ctypes.byref(ms), ctypes.byref(nmv), ctypes.byref(nk)))
         return ms.value, nmv.value, nk.value
+
+    def adjoint(self, c0, field, dt, nsteps, weights, scheme="rk4", order=4, hold=HOLD_LEFT, samples_per_step=1,
+                checkpoint_every=64, stream=None):
+        """Loss L = sum_a w_a |c_a(T)|^2 and dL/dfield by the discrete adjoint.
+
+        Returns (grad_field, c_final, loss) as CUDA tensors."""
+        c0 = _dev_c(c0, self.N, name="c0")
+        nF = self.nfield(nsteps, samples_per_step)
+        field = _dev_f64(field, nF, "field")
+        weights = _dev_f64(weights, self.N, "weights")
+        grad = torch.empty(nF, dtype=torch.float64, device=c0.device)
+        cT = torch.empty_like(c0)
+        loss = torch.empty(1, dtype=torch.float64, device=c0.device)
+        _check(_lib.tdse_adjoint(self._h, _ptr(c0), _ptr(field), int(samples_per_step), float(dt), int(nsteps),
+                                 SCHEMES[scheme], int(order), int(hold), _ptr(weights), int(checkpoint_every),
+                                 _ptr(grad), _ptr(cT), _ptr(loss), _stream(stream)))
+        return grad, cT, loss
+
+
+class FieldLoss(torch.autograd.Function):
+    """L(field) = sum_a w_a |c_a(T)|^2 for c(T) propagated from c0 under `field`,
+    differentiable with respect to the field samples.
+
+    The forward pass runs tdse_adjoint, which propagates with checkpoints and
+    returns the gradient together with the loss; backward scales that
+    gradient by the incoming grad.  Usage:
+        loss = FieldLoss.apply(field, H, c0, weights, dt, nsteps, opts)
+    with opts a dict of adjoint() keyword arguments."""
+
+    @staticmethod
+    def forward(ctx, field, H, c0, weights, dt, nsteps, opts=None):
+        grad, cT, loss = H.adjoint(c0, field.detach().contiguous(), dt, nsteps, weights, **(opts or {}))
+        ctx.save_for_backward(grad)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, gout):
+        (grad,) = ctx.saved_tensors
+        return gout * grad, None, None, None, None, None, None
