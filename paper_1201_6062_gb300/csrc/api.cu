@@ -9,6 +9,7 @@
 
 #include "tdse.h"
 #include "kernels.h"
+#include "batch.h"
 #include "plan.h"
 
 using tdse::SysDesc;
@@ -75,6 +76,8 @@ struct tdse_ctx {
     DevBuf hc, hfield;                 // device copies for the host-buffer entry point
     // adjoint: working state, checkpoints, stage store, cotangents, partial sums
     DevBuf ac, ckpt, store, aG, ag, agc, axq, dots, lparts;
+    // batched pulses: FP64 stage inputs / accumulators and the double-buffered product inputs
+    DevBuf bx, bacc, bq;
     MvPlan plan;
     SysDesc desc{};                    // host copy of the descriptor (static fields filled)
     SysDesc *stage = nullptr;          // pinned staging for descriptor uploads (2 slots)
@@ -486,9 +489,64 @@ tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, 
                                  double dt, long nsteps, tdse_scheme scheme, int taylor_order, int taylor_hold,
                                  void *stream)
 {
-    (void)ctx; (void)c; (void)field; (void)B; (void)samples_per_step; (void)dt; (void)nsteps; (void)scheme;
-    (void)taylor_order; (void)taylor_hold; (void)stream;
-    return fail(TDSE_ENOTSUP, "tdse_propagate_batch is not available in this build yet");
+    g_err.clear();
+    tdse_status st = check_prop_args(ctx, c, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold);
+    if (st != TDSE_OK) return st;
+    if (B < 1 || B > 65535) return fail(TDSE_EINVAL, "B must be in 1..65535");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = ctx->N;
+    const long S = (long)samples_per_step * nsteps + 1;
+    if (ctx->prec != TDSE_FP32) {
+        // FP64 / float-float products: the pulses run one after the other on
+        // the single-system path.
+        for (int b = 0; b < B; ++b) {
+            st = propagate_impl(ctx, c + 2 * (size_t)b * N, field + (size_t)b * S, samples_per_step, dt, nsteps,
+                                scheme, taylor_order, taylor_hold, s);
+            if (st != TDSE_OK) return st;
+        }
+        return TDSE_OK;
+    }
+    if (nsteps == 0) return TDSE_OK;
+    CUDA_TRY(ctx->bx.ensure(sizeof(double2) * (size_t)B * N));
+    CUDA_TRY(ctx->bacc.ensure(sizeof(double2) * (size_t)B * N));
+    CUDA_TRY(ctx->bq.ensure(sizeof(float) * 2 * 2 * (size_t)B * N));
+    float *q0 = ctx->bq.as<float>();
+    float *q1 = q0 + 2 * (size_t)B * N;
+    CUDA_TRY(tdse::launch_bprep_f32((const double2 *)c, q0, N, B, s));
+    ctx->launches += 1;
+    tdse::BatchArgs A{};
+    A.U = ctx->U.p;
+    A.bstride = ctx->bstride;
+    A.ld = ctx->ld;
+    A.n = ctx->n;
+    A.lmax = ctx->lmax;
+    A.B = B;
+    A.N = N;
+    A.E = ctx->E.as<double>();
+    A.field = field;
+    A.S = (int)S;
+    A.sps = samples_per_step;
+    A.c = (double2 *)c;
+    A.x = ctx->bx.as<double2>();
+    A.acc = ctx->bacc.as<double2>();
+    A.mode = scheme == TDSE_RK4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
+    A.order = taylor_order;
+    A.hold = taylor_hold;
+    A.dt = dt;
+    long t = 0;
+    for (long k = 0; k < nsteps; ++k) {
+        A.k = k;
+        const int q0s = scheme == TDSE_RK4 ? 0 : 1, q1s = scheme == TDSE_RK4 ? 3 : taylor_order;
+        for (int q = q0s; q <= q1s; ++q) {
+            A.stage = q;
+            A.xin = (t & 1) ? q1 : q0;
+            A.xout = (t & 1) ? q0 : q1;
+            CUDA_TRY(tdse::launch_bgemm_f32(A, s));
+            ctx->launches += 1;
+            ++t;
+        }
+    }
+    return TDSE_OK;
 }
 
 // Field samples that a stage's field value depends on, with weights

@@ -238,3 +238,17 @@ class FieldLoss(torch.autograd.Function):
     def backward(ctx, gout):
         (grad,) = ctx.saved_tensors
         return gout * grad, None, None, None, None, None, None
+
+
+def _batch_propagate(self, c, field, B, dt, nsteps, scheme="rk4", order=4, hold=HOLD_LEFT, samples_per_step=1,
+                     stream=None):
+    """Advance B states c [B, N] (in place) under their own fields field [B, S];
+    one Hamiltonian for all of them."""
+    c = _dev_c(c, self.N, B)
+    field = _dev_f64(field, B * self.nfield(nsteps, samples_per_step), "field")
+    _check(_lib.tdse_propagate_batch(self._h, _ptr(c), _ptr(field), int(B), int(samples_per_step), float(dt),
+                                     int(nsteps), SCHEMES[scheme], int(order), int(hold), _stream(stream)))
+    return c
+
+
+Hamiltonian.propagate_batch = _batch_propagate

@@ -1,0 +1,72 @@
+"""Batched pulses sharing one Hamiltonian, against the oracle run per pulse.
+Tolerances: the stated targets (1e-10 FP64-class, 1e-5 FP32 products)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1201_6062_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "df32": 1e-10, "fp32": 1e-5}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def sweep(lmax, n, B, nsteps, sps, dt=0.02, seed=3):
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, seed)
+    rng = np.random.default_rng(seed)
+    E0 = np.geomspace(0.05, 0.4, B)
+    om = rng.uniform(0.3, 0.9, B)
+    t0 = 3.0
+    F = np.stack([inputs.field_samples(E0[b], om[b], dt, nsteps, sps, cycles=3, t0=t0) for b in range(B)])
+    C0 = np.stack([inputs.random_state((lmax + 1) * n, seed + b) for b in range(B)])
+    return E, U, F, C0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "df32"])
+@pytest.mark.parametrize("lmax,n,B", [(3, 130, 5), (2, 1000, 64), (0, 40, 3), (4, 257, 1), (1, 17, 70)])
+def test_batched_rk4_matches_oracle_per_pulse(tdse_lib, prec, lmax, n, B):
+    if prec != "fp32" and B > 8:
+        pytest.skip("FP64-class batches run pulse by pulse; covered by the small cases")
+    dt, nsteps, sps = 0.02, 40, 1
+    E, U, F, C0 = sweep(lmax, n, B, nsteps, sps)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, prec)
+    c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(c, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps)
+    got = c.cpu().numpy().reshape(B, -1)
+    for b in range(B):
+        ref, _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, nsteps)
+        assert rel(got[b], ref) < TOL[prec], b
+
+
+@pytest.mark.parametrize("K,hold,sps", [(6, 0, 1), (5, 1, 2)])
+def test_batched_taylor_matches_oracle(tdse_lib, K, hold, sps):
+    lmax, n, B, dt, nsteps = 3, 300, 7, 0.02, 25
+    E, U, F, C0 = sweep(lmax, n, B, nsteps, sps)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "fp32")
+    c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(c, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps, "taylor", order=K, hold=hold,
+                      samples_per_step=sps)
+    got = c.cpu().numpy().reshape(B, -1)
+    for b in range(B):
+        ref, _ = oracle.taylor(lmax, n, E, U, C0[b], F[b], dt, nsteps, K, samples_per_step=sps, hold=hold)
+        assert rel(got[b], ref) < 1e-5, b
+
+
+def test_batched_equals_single_instance_fp32_per_pulse_within_rounding(tdse_lib):
+    """The batched FP32 GEMM and the single-instance FP32 mat-vec sum in
+    different orders; both stay within the FP32-product tolerance of each other."""
+    lmax, n, B, dt, nsteps = 2, 600, 4, 0.02, 30
+    E, U, F, C0 = sweep(lmax, n, B, nsteps, 1)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "fp32")
+    cb = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(cb, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps)
+    for b in range(B):
+        c = torch.from_numpy(C0[b].copy()).cuda()
+        H.propagate(c, torch.from_numpy(F[b]).cuda(), dt, nsteps)
+        assert rel(cb.view(B, -1)[b].cpu().numpy(), c.cpu().numpy()) < 1e-5
