@@ -65,6 +65,27 @@ def peaks():
 
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
+KERNEL_SOURCES = ["paper_1201_6062_gb300/csrc/mvt.cu", "paper_1201_6062_gb300/csrc/common.cuh",
+                  "paper_1201_6062_gb300/csrc/sync.cuh"]
+
+
+def profiled_traffic(prec):
+    """DRAM bytes per launch of the block mat-vec from the committed ncu
+    summary, or None when the kernel sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "mvt_%s_large.md" % prec)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.split(":", 1)[0] in ("traffic_bytes_per_launch", "source_sha256"):
+            k, v = line.split(":", 1)
+            fields[k] = v.strip()
+    h = hashlib.sha256(b"".join(open(os.path.join(ROOT, p), "rb").read() for p in KERNEL_SOURCES)).hexdigest()
+    if fields.get("source_sha256") != h or "traffic_bytes_per_launch" not in fields:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
 
 class ClockSampler:
     """nvidia-smi clock/throttle samples over the timed region."""
@@ -295,6 +316,8 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": p["mv_gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": p["mv_gbs"] / hbm_peak, "traffic": None, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
     roof["kernel"] = "mvt_kernel<%s> (block mat-vec, bulk-copy ring)" % primary
+    roof["traffic"] = profiled_traffic(primary)
+    roof["traffic_source"] = "profiles/mvt_%s_large.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)" % primary
     roof["alg_bytes_per_launch"] = p["alg_bytes_per_launch"]
 
     e2e = None

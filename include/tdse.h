@@ -268,12 +268,29 @@ void tdse_group_destroy(tdse_group *g);
 /*
  * c_ptrs[s]      device, complex [N_s] state of system s (in/out).
  * field_ptrs[s]  device, FP64 [samples_per_step*nsteps + 1] field of system s.
- * Both arrays are host arrays of `count` device pointers.  RK4 only.
- * Errors: EINVAL, ECUDA, ENOTSUP.
+ * Both arrays are host arrays of `count` device pointers.  RK4 only.  Each
+ * stage is one block-product launch and one epilogue launch for all systems;
+ * one step is captured once into a CUDA graph (re-captured when dt or
+ * samples_per_step change) and replayed nsteps times.  The systems' own
+ * scratch vectors are used, so a context must not be propagated on its own
+ * while its group runs.  Errors: EINVAL, ECUDA.
  */
 tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs,
                                  const double *const *field_ptrs, int samples_per_step,
                                  double dt, long nsteps, void *stream);
+
+/* As tdse_sync, for a group (also reports the member kernels' timeouts). */
+tdse_status tdse_group_sync(tdse_group *g, void *stream);
+
+/*
+ * tdse_group_tune — autotuner: times `reps` block-product launches for every
+ * valid ring-stage depth (1, 2, 4, 8 rows per bulk copy) on the group's own
+ * plan and keeps the fastest for later tdse_group_propagate calls.  Reports
+ * the choice and its time per launch (either pointer may be NULL).  Clobbers
+ * the members' scratch vectors; synchronises `stream`.
+ * Errors: EINVAL, ECUDA, ETIMEOUT.
+ */
+tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *best_ms, void *stream);
 
 #ifdef __cplusplus
 }

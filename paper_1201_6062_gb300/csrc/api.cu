@@ -63,6 +63,7 @@ struct DevBuf {
 struct MvPlan {
     tdse::MvCfg cfg{};
     int grid = 0;
+    int max_ld = 0;        // largest row stride among the systems
     int nblk = 0;          // epilogue blocks
     DevBuf segs, cta_off, blk;
 };
@@ -119,6 +120,7 @@ static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std:
         rows += (long long)lmax[s] * n[s];
     }
     const int ldmax = (nmax + 3) & ~3;
+    mp.max_ld = ldmax;
     int G;
     if (tdse::mvt_config(prec, nmax, ldmax, &mp.cfg)) {
         G = sm_count();                         // one ring CTA per SM (shared memory bound)
@@ -701,23 +703,241 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
 }
 
 struct tdse_group {
-    int dummy;
+    std::vector<tdse_ctx *> sys;
+    int prec = 0;
+    MvPlan plan;
+    std::vector<DevBuf> P, sb;          // per-system column-partial slots and slot starts
+    std::vector<SysDesc> desc;          // per-system descriptors (static fields filled)
+    DevBuf ddesc;                       // device descriptor table
+    DevBuf errw;
+    DevBuf kdev;                        // device step counter read by the captured step graph
+    SysDesc *stage = nullptr;
+    cudaEvent_t stage_ev = nullptr;
+    bool stage_pending = false;
+    long launches = 0;
+    int tuned_rs = 0;                   // rows per ring stage chosen by tdse_group_tune (0: default)
+    // captured one-step graph (valid for graph_dt / graph_sps)
+    cudaGraphExec_t gexec = nullptr;
+    double graph_dt = 0.0;
+    int graph_sps = 0;
+    ~tdse_group()
+    {
+        cudaDeviceSynchronize();
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (stage) cudaFreeHost(stage);
+        if (stage_ev) cudaEventDestroy(stage_ev);
+    }
 };
 
 tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **out)
 {
-    (void)systems; (void)count;
-    if (out) *out = nullptr;
-    return fail(TDSE_ENOTSUP, "groups are not available in this build yet");
+    g_err.clear();
+    if (!out) return fail(TDSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!systems || count < 1 || count > 4096) return fail(TDSE_EINVAL, "need 1 <= count <= 4096 systems");
+    for (int i = 0; i < count; ++i) {
+        if (!systems[i]) return fail(TDSE_EINVAL, "systems[%d] is NULL", i);
+        if (systems[i]->prec != systems[0]->prec) return fail(TDSE_EINVAL, "all systems must share one precision");
+        for (int j = 0; j < i; ++j)
+            if (systems[j] == systems[i]) return fail(TDSE_EINVAL, "systems[%d] repeats systems[%d]", i, j);
+    }
+    tdse_group *g = new (std::nothrow) tdse_group();
+    if (!g) return fail(TDSE_ENOMEM, "host allocation failed");
+    auto bail = [&](tdse_status st) { delete g; return st; };
+    g->sys.assign(systems, systems + count);
+    g->prec = systems[0]->prec;
+    std::vector<int> lm(count), nn(count);
+    for (int i = 0; i < count; ++i) { lm[i] = systems[i]->lmax; nn[i] = systems[i]->n; }
+    tdse::Plan plan;
+    tdse_status st = build_plan(g->prec, lm, nn, g->plan, plan);
+    if (st != TDSE_OK) return bail(st);
+    g->P.resize(count);
+    g->sb.resize(count);
+    g->desc.resize(count);
+    for (int i = 0; i < count; ++i) {
+        tdse_ctx *c = systems[i];
+        const size_t ns = (size_t)(plan.nslots[i] > 0 ? plan.nslots[i] : 1);
+        cudaError_t e = g->P[i].ensure(sizeof(double2) * ns * c->n);
+        if (e == cudaSuccess) e = g->sb[i].ensure(sizeof(int) * (c->lmax + 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->sb[i].p, plan.sb[i].data(), sizeof(int) * (c->lmax + 1), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(fail(TDSE_ECUDA, "group buffers: %s", cudaGetErrorString(e)));
+        SysDesc d = c->desc;
+        d.P = g->P[i].as<double2>();
+        d.sb = g->sb[i].as<int>();
+        g->desc[i] = d;
+    }
+    cudaError_t e = g->ddesc.ensure(sizeof(SysDesc) * count);
+    if (e == cudaSuccess) e = g->errw.ensure(sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(g->errw.p, 0, sizeof(int));
+    if (e == cudaSuccess) e = g->kdev.ensure(sizeof(long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->stage, sizeof(SysDesc) * count);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->stage_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(fail(TDSE_ECUDA, "group set-up: %s", cudaGetErrorString(e)));
+    *out = g;
+    return TDSE_OK;
 }
 
 void tdse_group_destroy(tdse_group *g) { delete g; }
 
+static tdse_status group_product(tdse_group *g, cudaStream_t s, const tdse::MvCfg &cfg)
+{
+    if (g->plan.grid <= 0) return TDSE_OK;
+    if (cfg.tma)
+        CUDA_TRY(tdse::launch_mvt(g->prec, cfg, g->plan.grid, g->ddesc.as<SysDesc>(), g->plan.segs.as<Seg>(),
+                                  g->plan.cta_off.as<int>(), g->errw.as<int>(), s));
+    else
+        CUDA_TRY(tdse::launch_mv(g->prec, cfg, g->plan.grid, g->ddesc.as<SysDesc>(), g->plan.segs.as<Seg>(),
+                                 g->plan.cta_off.as<int>(), s));
+    return TDSE_OK;
+}
+
+static tdse::MvCfg group_cfg(tdse_group *g)
+{
+    tdse::MvCfg cfg = g->plan.cfg;
+    if (cfg.tma && g->tuned_rs > 0) cfg.RS = g->tuned_rs;
+    return cfg;
+}
+
+// Enqueue one RK4 step (4 products + 4 epilogues + the step-counter bump);
+// the epilogues read the step index from g->kdev.
+static tdse_status group_step(tdse_group *g, int sps, double dt, cudaStream_t s)
+{
+    const tdse::MvCfg cfg = group_cfg(g);
+    tdse::EpiArgs a{};
+    a.mode = tdse::EPI_RK4;
+    a.sps = sps;
+    a.dt = dt;
+    a.kdev = g->kdev.as<long long>();
+    for (int q = 0; q < 4; ++q) {
+        a.stage = q;
+        tdse_status st = group_product(g, s, cfg);
+        if (st != TDSE_OK) return st;
+        CUDA_TRY(tdse::launch_epi(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->ddesc.as<SysDesc>(), a, s));
+    }
+    CUDA_TRY(tdse::launch_bump(g->kdev.as<long long>(), s));
+    return TDSE_OK;
+}
+
 tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const double *const *field_ptrs,
                                  int samples_per_step, double dt, long nsteps, void *stream)
 {
-    (void)g; (void)c_ptrs; (void)field_ptrs; (void)samples_per_step; (void)dt; (void)nsteps; (void)stream;
-    return fail(TDSE_ENOTSUP, "groups are not available in this build yet");
+    g_err.clear();
+    if (!g || !c_ptrs || !field_ptrs) return fail(TDSE_EINVAL, "NULL argument");
+    if (samples_per_step != 1 && samples_per_step != 2) return fail(TDSE_EINVAL, "samples_per_step must be 1 or 2");
+    if (!(dt == dt) || dt == 0.0 || dt > 1e300 || dt < -1e300) return fail(TDSE_EINVAL, "dt must be finite and nonzero");
+    if (nsteps < 0) return fail(TDSE_EINVAL, "nsteps must be >= 0");
+    const int count = (int)g->sys.size();
+    for (int i = 0; i < count; ++i) {
+        if (!c_ptrs[i] || !field_ptrs[i]) return fail(TDSE_EINVAL, "c_ptrs[%d] or field_ptrs[%d] is NULL", i, i);
+        if (!aligned16(c_ptrs[i])) return fail(TDSE_EINVAL, "c_ptrs[%d] must be 16-byte aligned", i);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->stage_pending) CUDA_TRY(cudaEventSynchronize(g->stage_ev));
+    for (int i = 0; i < count; ++i) {
+        g->stage[i] = g->desc[i];
+        g->stage[i].c = (double2 *)c_ptrs[i];
+        g->stage[i].field = field_ptrs[i];
+    }
+    CUDA_TRY(cudaMemcpyAsync(g->ddesc.p, g->stage, sizeof(SysDesc) * count, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaEventRecord(g->stage_ev, s));
+    g->stage_pending = true;
+    if (nsteps == 0) return TDSE_OK;
+    CUDA_TRY(cudaMemsetAsync(g->kdev.p, 0, sizeof(long long), s));
+    CUDA_TRY(tdse::launch_prep(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->ddesc.as<SysDesc>(), 0, s));
+    // One step is captured once into a CUDA graph and replayed nsteps times.
+    if (!g->gexec || g->graph_dt != dt || g->graph_sps != samples_per_step) {
+        if (g->gexec) { cudaGraphExecDestroy(g->gexec); g->gexec = nullptr; }
+        const tdse::MvCfg cfg = group_cfg(g);
+        if (cfg.tma && g->plan.grid > 0) CUDA_TRY(tdse::mvt_prepare(g->prec, cfg));
+        cudaStream_t cs;
+        CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        tdse_status st = TDSE_OK;
+        if (e == cudaSuccess) {
+            st = group_step(g, samples_per_step, dt, cs);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        if (e == cudaSuccess && st == TDSE_OK) e = cudaGraphInstantiate(&g->gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (st != TDSE_OK) return st;
+        if (e != cudaSuccess) return fail(TDSE_ECUDA, "step graph capture: %s", cudaGetErrorString(e));
+        g->graph_dt = dt;
+        g->graph_sps = samples_per_step;
+    }
+    for (long k = 0; k < nsteps; ++k) CUDA_TRY(cudaGraphLaunch(g->gexec, s));
+    g->launches += 1 + nsteps * (4 * ((g->plan.grid > 0) + 1) + 1);
+    return TDSE_OK;
+}
+
+tdse_status tdse_group_sync(tdse_group *g, void *stream)
+{
+    if (!g) return fail(TDSE_EINVAL, "NULL group");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    int w = 0;
+    CUDA_TRY(cudaMemcpy(&w, g->errw.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (w) {
+        CUDA_TRY(cudaMemset(g->errw.p, 0, sizeof(int)));
+        return fail(TDSE_ETIMEOUT, "a bounded device-side wait gave up (status word 0x%x)", w);
+    }
+    return TDSE_OK;
+}
+
+tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *best_ms, void *stream)
+{
+    g_err.clear();
+    if (!g) return fail(TDSE_EINVAL, "NULL group");
+    if (reps < 1) reps = 3;
+    cudaStream_t s = (cudaStream_t)stream;
+    tdse::MvCfg base = g->plan.cfg;
+    if (!base.tma || g->plan.grid <= 0) {
+        if (chosen_rs) *chosen_rs = 0;
+        if (best_ms) *best_ms = 0.0;
+        return TDSE_OK;
+    }
+    // The descriptors must point at valid state buffers: use each system's own scratch.
+    if (g->stage_pending) CUDA_TRY(cudaEventSynchronize(g->stage_ev));
+    const int count = (int)g->sys.size();
+    for (int i = 0; i < count; ++i) {
+        g->stage[i] = g->desc[i];
+        g->stage[i].c = g->desc[i].x;
+        g->stage[i].field = nullptr;
+    }
+    CUDA_TRY(cudaMemcpyAsync(g->ddesc.p, g->stage, sizeof(SysDesc) * count, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaEventRecord(g->stage_ev, s));
+    g->stage_pending = true;
+    CUDA_TRY(tdse::launch_prep(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->ddesc.as<SysDesc>(), 1, s));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int best = base.RS;
+    double bestt = 1e300;
+    for (int rs = 1; rs <= 8; rs *= 2) {
+        tdse::MvCfg cfg = base;
+        if (!tdse::mvt_rs_valid(g->prec, cfg, rs, g->plan.max_ld)) continue;
+        cfg.RS = rs;
+        tdse_status st = group_product(g, s, cfg);          // warm-up
+        if (st != TDSE_OK) return st;
+        CUDA_TRY(cudaEventRecord(e0, s));
+        for (int r = 0; r < reps; ++r) {
+            st = group_product(g, s, cfg);
+            if (st != TDSE_OK) return st;
+        }
+        CUDA_TRY(cudaEventRecord(e1, s));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / reps < bestt) { bestt = ms / reps; best = rs; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->tuned_rs = best;
+    if (g->gexec) { cudaGraphExecDestroy(g->gexec); g->gexec = nullptr; }
+    if (chosen_rs) *chosen_rs = best;
+    if (best_ms) *best_ms = bestt;
+    return tdse_group_sync(g, stream);
 }
 
 }  // extern "C"

@@ -24,6 +24,10 @@ int mv_ctas_per_sm(int prec, const MvCfg &cfg);
 // Ring-fed variant for rows of more than 128 column groups; false if n/ld do
 // not qualify.
 bool mvt_config(int prec, int n, int ld, MvCfg *out);
+// Sets the kernel attributes a launch needs (call outside stream capture).
+cudaError_t mvt_prepare(int prec, const MvCfg &cfg);
+// Whether `rs` rows per stage fit the ring for rows of `ld` elements.
+bool mvt_rs_valid(int prec, const MvCfg &cfg, int rs, int ld);
 cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys, const Seg *segs,
                        const int *cta_off, int *err, cudaStream_t stream);
 
@@ -49,7 +53,10 @@ struct EpiArgs {
     double fval;    // field for EPI_HX / EPI_MIHX
     double2 *st_x;  // if set: also store this stage's new x (next stage input / Taylor term)
     double2 *st_c;  // if set: also store the new c (last RK4 stage / last Taylor term)
+    const long long *kdev;   // if set: the step index is *kdev (captured step graphs)
 };
+// *kdev += 1 (one thread): advances the step index of a captured step graph.
+cudaError_t launch_bump(long long *kdev, cudaStream_t stream);
 cudaError_t launch_epi(int prec, int nblk, const int2 *blk, const SysDesc *sys,
                        EpiArgs a, cudaStream_t stream);
 

@@ -263,6 +263,7 @@ epi_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, EpiArg
     const SysDesc &S = sys[bm.x];
     const long long a = (long long)bm.y + threadIdx.x;
     if (a >= S.N) return;
+    if (A.kdev) A.k = *A.kdev;
     const int n = S.n;
     const int m = (int)(a / n), i = (int)(a - (long long)m * n);
     double dr = 0.0, di = 0.0;
@@ -360,6 +361,14 @@ cudaError_t launch_epi(int prec, int nblk, const int2 *blk, const SysDesc *sys, 
     case 2: epi_kernel<PolDF32><<<nblk, 256, 0, stream>>>(sys, blk, a); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+__global__ void bump_kernel(long long *kdev) { *kdev += 1; }
+
+cudaError_t launch_bump(long long *kdev, cudaStream_t stream)
+{
+    bump_kernel<<<1, 1, 0, stream>>>(kdev);
     return cudaGetLastError();
 }
 

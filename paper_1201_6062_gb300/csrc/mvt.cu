@@ -293,6 +293,20 @@ bool mvt_config(int prec, int n, int ld, MvCfg *out)
     return false;
 }
 
+bool mvt_rs_valid(int prec, const MvCfg &cfg, int rs, int ld)
+{
+    if (rs != 1 && rs != 2 && rs != 4 && rs != 8) return false;
+    if ((long long)rs * ld * elem_size(prec) > STAGE_MAX) return false;
+    return mvt_fn_prec(prec, cfg.idx, rs) != nullptr;
+}
+
+cudaError_t mvt_prepare(int prec, const MvCfg &cfg)
+{
+    const void *fn = mvt_fn_prec(prec, cfg.idx, cfg.RS);
+    if (!fn) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, NS * STAGE_MAX);
+}
+
 cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys, const Seg *segs,
                        const int *cta_off, int *err, cudaStream_t stream)
 {

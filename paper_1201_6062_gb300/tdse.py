@@ -252,3 +252,55 @@ def _batch_propagate(self, c, field, B, dt, nsteps, scheme="rk4", order=4, hold=
 
 
 Hamiltonian.propagate_batch = _batch_propagate
+
+
+_lib.tdse_group_sync.argtypes = [_vp, _vp]
+_lib.tdse_group_sync.restype = _i
+_lib.tdse_group_tune.argtypes = [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]
+_lib.tdse_group_tune.restype = _i
+
+
+class Group:
+    """Several Hamiltonians of different (lmax, n) advanced together: one
+    launch per stage for all of them (uneven batch).  The member Hamiltonians
+    must outlive the group and must not be propagated on their own while the
+    group runs (their scratch vectors are shared)."""
+
+    def __init__(self, hams):
+        self.hams = list(hams)
+        arr = (_vp * len(self.hams))(*[h.handle for h in self.hams])
+        g = _vp()
+        _check(_lib.tdse_group_create(arr, len(self.hams), ctypes.byref(g)))
+        self._g = g
+
+    def close(self):
+        if getattr(self, "_g", None):
+            _lib.tdse_group_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def propagate(self, cs, fields, dt, nsteps, samples_per_step=1, stream=None):
+        if len(cs) != len(self.hams) or len(fields) != len(self.hams):
+            raise ValueError("need one state and one field per system")
+        for h, c, f in zip(self.hams, cs, fields):
+            _dev_c(c, h.N)
+            _dev_f64(f, h.nfield(nsteps, samples_per_step), "field")
+        ca = (_vp * len(cs))(*[c.data_ptr() for c in cs])
+        fa = (_vp * len(fields))(*[f.data_ptr() for f in fields])
+        _check(_lib.tdse_group_propagate(self._g, ca, fa, int(samples_per_step), float(dt), int(nsteps),
+                                         _stream(stream)))
+        return cs
+
+    def sync(self, stream=None):
+        _check(_lib.tdse_group_sync(self._g, _stream(stream)))
+
+    def tune(self, reps=3, stream=None):
+        """Autotune the ring-stage depth; returns (rows per stage, ms per product)."""
+        rs, ms = _i(), _d()
+        _check(_lib.tdse_group_tune(self._g, int(reps), ctypes.byref(rs), ctypes.byref(ms), _stream(stream)))
+        return rs.value, ms.value
