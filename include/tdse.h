@@ -66,9 +66,13 @@ typedef enum {
  *   TDSE_DF32   U stored as an FP32 (hi, lo) pair, products and sums in
  *               float-float arithmetic (about 44 significant bits) on the
  *               FP32 pipe; FP64-class accuracy without FP64 multiplies.
- *   TDSE_BF16X3 batched paths only: U and the batched state split into
- *               bf16 (hi, lo) pairs, three tensor-core products with FP32
- *               accumulation.
+ *   TDSE_BF16X3 tdse_propagate_batch only (other entry points return
+ *               TDSE_ENOTSUP, tdse_populations/tdse_norm excepted): U, U^T
+ *               and the batched states split into bf16 (hi, lo) pairs, three
+ *               tcgen05 tensor-core products (hh + hl + lh) with FP32
+ *               accumulation; the batched state between stages is
+ *               float-float (FP32 hi + lo) instead of FP64, because the FP64
+ *               pipe of this GPU would cost more than the products.
  */
 typedef enum {
     TDSE_FP64 = 0,

@@ -7,10 +7,15 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
 #include "tdse.h"
 #include "kernels.h"
 #include "batch.h"
 #include "plan.h"
+#include "tc.h"
 
 using tdse::SysDesc;
 using tdse::Seg;
@@ -79,6 +84,12 @@ struct tdse_ctx {
     DevBuf ac, ckpt, store, aG, ag, agc, axq, dots, lparts;
     // batched pulses: FP64 stage inputs / accumulators and the double-buffered product inputs
     DevBuf bx, bacc, bq;
+    // bf16x3 tensor-core path: dipole planes, energies as float-float, float-float
+    // states, double-buffered bf16 state planes and their TMA descriptors
+    DevBuf tU, tEdf, tc_c, tc_x, tc_acc, tc_planes, tc_fdf;
+    int nb = 0, ldb = 0;
+    int tc_B = 0;                       // batch size the plane buffers / maps were built for
+    tdse::TcMaps tc_maps[2];            // [input buffer]
     MvPlan plan;
     SysDesc desc{};                    // host copy of the descriptor (static fields filled)
     SysDesc *stage = nullptr;          // pinned staging for descriptor uploads (2 slots)
@@ -152,6 +163,171 @@ static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std:
     return TDSE_OK;
 }
 
+// ---------------------------------------------------------------- bf16x3 --
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static void *fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+    }
+    return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+}
+
+// bf16 tensor map with a 128-byte-swizzled box {64, rows(, 1)}; zero fill outside.
+static tdse_status make_map(CUtensorMap *m, void *base, int rank, const cuuint64_t *dims, const cuuint64_t *strides,
+                            const cuuint32_t *box)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(TDSE_ECUDA, "cuTensorMapEncodeTiled is not available");
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(TDSE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return TDSE_OK;
+}
+
+static tdse::df host_df(double v)
+{
+    const float h = (float)v;
+    return tdse::df{h, (float)(v - (double)h)};
+}
+
+// Context of precision BF16X3: energies (FP64 and float-float), the dipole
+// blocks and their transposes as bf16 (hi, lo) planes with TMA descriptors.
+static tdse_status create_tc(tdse_ctx *c, const double *energies, const double *U)
+{
+    const int lmax = c->lmax, n = c->n;
+    c->ldb = (n + 7) & ~7;                    // 16-byte row stride for the tensor maps
+    c->nb = (n + 63) & ~63;                   // state-plane block stride: TMA x coordinates stay 64-aligned
+    CUDA_TRY(c->E.ensure(sizeof(double) * c->N));
+    CUDA_TRY(cudaMemcpy(c->E.p, energies, sizeof(double) * c->N, cudaMemcpyHostToDevice));
+    std::vector<float2> edf((size_t)c->N);
+    for (long a = 0; a < c->N; ++a) { tdse::df d = host_df(energies[a]); edf[(size_t)a] = make_float2(d.h, d.l); }
+    CUDA_TRY(c->tEdf.ensure(sizeof(float2) * c->N));
+    CUDA_TRY(cudaMemcpy(c->tEdf.p, edf.data(), sizeof(float2) * c->N, cudaMemcpyHostToDevice));
+    const size_t plane = (size_t)(lmax > 0 ? lmax : 1) * n * c->ldb;     // elements per dipole plane
+    CUDA_TRY(c->tU.ensure(sizeof(__nv_bfloat16) * 4 * plane));
+    CUDA_TRY(cudaMemset(c->tU.p, 0, sizeof(__nv_bfloat16) * 4 * plane));
+    __nv_bfloat16 *dU = c->tU.as<__nv_bfloat16>();
+    if (lmax > 0) {
+        std::vector<__nv_bfloat16> hb(4 * plane, __float2bfloat16(0.f));
+        for (int l = 0; l < lmax; ++l)
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    const double v = U[((size_t)l * n + i) * n + j];
+                    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+                    const __nv_bfloat16 lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+                    const size_t q = ((size_t)l * n + i) * c->ldb + j;     // U_l[i][j]
+                    const size_t t = ((size_t)l * n + j) * c->ldb + i;     // U_l^T[j][i]
+                    hb[q] = h;
+                    hb[plane + q] = lo;
+                    hb[2 * plane + t] = h;
+                    hb[3 * plane + t] = lo;
+                }
+        CUDA_TRY(cudaMemcpy(dU, hb.data(), sizeof(__nv_bfloat16) * 4 * plane, cudaMemcpyHostToDevice));
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)(lmax > 0 ? lmax : 1)};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->ldb * 2, (cuuint64_t)n * c->ldb * 2};
+    const cuuint32_t box[3] = {64, 128, 1};
+    for (int b = 0; b < 2; ++b) {
+        tdse_status st = make_map(&c->tc_maps[b].Uh, dU, 3, dims, strides, box);
+        if (st == TDSE_OK) st = make_map(&c->tc_maps[b].Ul, dU + plane, 3, dims, strides, box);
+        if (st == TDSE_OK) st = make_map(&c->tc_maps[b].Th, dU + 2 * plane, 3, dims, strides, box);
+        if (st == TDSE_OK) st = make_map(&c->tc_maps[b].Tl, dU + 3 * plane, 3, dims, strides, box);
+        if (st != TDSE_OK) return st;
+    }
+    CUDA_TRY(c->sys.ensure(2 * sizeof(SysDesc)));
+    CUDA_TRY(c->errw.ensure(sizeof(int)));
+    CUDA_TRY(cudaMemset(c->errw.p, 0, sizeof(int)));
+    CUDA_TRY(cudaMallocHost((void **)&c->stage, 2 * sizeof(SysDesc)));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
+    c->desc.n = n; c->desc.lmax = lmax; c->desc.N = c->N; c->desc.E = c->E.as<double>();
+    return TDSE_OK;
+}
+
+// Batch of B pulses on the tensor cores (bf16x3 products, float-float state).
+static tdse_status propagate_batch_tc(tdse_ctx *ctx, double *c, const double *field, int B, int sps, double dt,
+                                      long nsteps, tdse_scheme scheme, int order, int hold, cudaStream_t s)
+{
+    const long long N = ctx->N;
+    const int L = ctx->lmax + 1;
+    const long long plane = (long long)L * ctx->nb;
+    if (2LL * B > 0x7fffffffLL / 2) return fail(TDSE_EINVAL, "batch too large");
+    if (ctx->tc_B != B) {
+        CUDA_TRY(ctx->tc_c.ensure(sizeof(float4) * (size_t)B * N));
+        CUDA_TRY(ctx->tc_x.ensure(sizeof(float4) * (size_t)B * N));
+        CUDA_TRY(ctx->tc_acc.ensure(sizeof(float4) * (size_t)B * N));
+        const size_t pb = sizeof(__nv_bfloat16) * 2 * (size_t)B * plane;      // one (h or l) plane set
+        CUDA_TRY(ctx->tc_planes.ensure(4 * pb));
+        CUDA_TRY(cudaMemsetAsync(ctx->tc_planes.p, 0, 4 * pb, s));                // padding columns stay zero
+        __nv_bfloat16 *base = ctx->tc_planes.as<__nv_bfloat16>();
+        const cuuint64_t dims[2] = {(cuuint64_t)plane, (cuuint64_t)(2 * B)};
+        const cuuint64_t strides[1] = {(cuuint64_t)plane * 2};
+        const cuuint32_t box[2] = {64, 256};
+        for (int b = 0; b < 2; ++b) {
+            tdse_status st = make_map(&ctx->tc_maps[b].Xh, base + (size_t)(2 * b) * 2 * B * plane, 2, dims, strides, box);
+            if (st == TDSE_OK)
+                st = make_map(&ctx->tc_maps[b].Xl, base + (size_t)(2 * b + 1) * 2 * B * plane, 2, dims, strides, box);
+            if (st != TDSE_OK) return st;
+        }
+        ctx->tc_B = B;
+    }
+    CUDA_TRY(ctx->tc_fdf.ensure(sizeof(float2) * 3 * (size_t)B * nsteps));
+    CUDA_TRY(tdse::launch_tc_field(field, (int)((long)sps * nsteps + 1), sps, nsteps, B, ctx->tc_fdf.as<float2>(), s));
+    ctx->launches += 1;
+    __nv_bfloat16 *base = ctx->tc_planes.as<__nv_bfloat16>();
+    auto plane_h = [&](int b) { return base + (size_t)(2 * b) * 2 * B * plane; };
+    auto plane_l = [&](int b) { return base + (size_t)(2 * b + 1) * 2 * B * plane; };
+    CUDA_TRY(tdse::launch_tc_in((const double2 *)c, ctx->tc_c.as<float4>(), plane_h(0), plane_l(0), N, ctx->n,
+                                ctx->nb, plane, B, s));
+    ctx->launches += 1;
+    tdse::TcArgs A{};
+    A.n = ctx->n;
+    A.lmax = ctx->lmax;
+    A.B = B;
+    A.nb = ctx->nb;
+    A.N = N;
+    A.plane = plane;
+    A.S = (int)((long)sps * nsteps + 1);
+    A.sps = sps;
+    A.mode = scheme == TDSE_RK4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
+    A.order = order;
+    A.hold = hold;
+    A.half_dt = host_df(0.5 * dt);
+    A.full_dt = host_df(dt);
+    A.sixth_dt = host_df(dt / 6.0);
+    A.Edf = ctx->tEdf.as<float2>();
+    A.field = field;
+    A.c = ctx->tc_c.as<float4>();
+    A.x = ctx->tc_x.as<float4>();
+    A.acc = ctx->tc_acc.as<float4>();
+    A.err = ctx->errw.as<int>();
+    long t = 0;
+    for (long k = 0; k < nsteps; ++k) {
+        A.k = k;
+        const int q0 = scheme == TDSE_RK4 ? 0 : 1, q1 = scheme == TDSE_RK4 ? 3 : order;
+        for (int q = q0; q <= q1; ++q) {
+            A.stage = q;
+            if (scheme != TDSE_RK4) A.term_dt = host_df(dt / (double)q);
+            const int h = scheme == TDSE_RK4 ? (q == 0 ? 0 : (q == 3 ? 2 : 1)) : (hold ? 1 : 0);
+            A.fdf = ctx->tc_fdf.as<float2>() + ((size_t)k * 3 + h) * B;
+            const int in = (int)(t & 1);
+            A.xo_h = plane_h(in ^ 1);
+            A.xo_l = plane_l(in ^ 1);
+            CUDA_TRY(tdse::launch_tc(ctx->tc_maps[in], A, s));
+            ctx->launches += 1;
+            ++t;
+        }
+    }
+    CUDA_TRY(tdse::launch_tc_out(ctx->tc_c.as<float4>(), (double2 *)c, N * B, s));
+    ctx->launches += 1;
+    return TDSE_OK;
+}
+
 extern "C" {
 
 int tdse_version(void) { return 1 * 10000 + 0 * 100 + 0; }
@@ -169,11 +345,17 @@ tdse_status tdse_create(const double *energies, const double *dipole_blocks, int
     if (!energies) return fail(TDSE_EINVAL, "energies is NULL");
     if (lmax < 0 || n < 1 || n > 4096) return fail(TDSE_EINVAL, "need lmax >= 0 and 1 <= n <= 4096 (lmax=%d n=%d)", lmax, n);
     if (lmax > 0 && !dipole_blocks) return fail(TDSE_EINVAL, "dipole_blocks is NULL with lmax=%d", lmax);
-    if (prec != TDSE_FP64 && prec != TDSE_FP32 && prec != TDSE_DF32)
-        return fail(TDSE_ENOTSUP, "precision %d is only available on batched paths", (int)prec);
+    if (prec != TDSE_FP64 && prec != TDSE_FP32 && prec != TDSE_DF32 && prec != TDSE_BF16X3)
+        return fail(TDSE_EINVAL, "unknown precision %d", (int)prec);
     tdse_ctx *c = new (std::nothrow) tdse_ctx();
     if (!c) return fail(TDSE_ENOMEM, "host allocation failed");
     c->lmax = lmax; c->n = n; c->N = (lmax + 1) * n; c->prec = prec;
+    if (prec == TDSE_BF16X3) {
+        tdse_status st = create_tc(c, energies, dipole_blocks);
+        if (st != TDSE_OK) { delete c; return st; }
+        *out = c;
+        return TDSE_OK;
+    }
     c->ld = (n + 3) & ~3;
     const int eb = elem_bytes(prec);
     long long blk_elems = (long long)n * c->ld;
@@ -311,6 +493,7 @@ tdse_status tdse_hmatvec(tdse_ctx *ctx, double f, const double *x, double *y, in
 {
     g_err.clear();
     if (!ctx || !x || !y) return fail(TDSE_EINVAL, "NULL argument");
+    if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
     if (!aligned16(x) || !aligned16(y)) return fail(TDSE_EINVAL, "x and y must be 16-byte aligned");
     if (x == y) return fail(TDSE_EINVAL, "x and y must not alias");
     cudaStream_t s = (cudaStream_t)stream;
@@ -385,6 +568,7 @@ tdse_status tdse_propagate(tdse_ctx *ctx, double *c, const double *field, int sa
     g_err.clear();
     tdse_status st = check_prop_args(ctx, c, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold);
     if (st != TDSE_OK) return st;
+    if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
     return propagate_impl(ctx, c, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold,
                           (cudaStream_t)stream);
 }
@@ -397,6 +581,7 @@ tdse_status tdse_propagate_host(tdse_ctx *ctx, double *c_host, const double *fie
     if (!ctx || !c_host || !field_host) return fail(TDSE_EINVAL, "NULL argument");
     if (samples_per_step != 1 && samples_per_step != 2) return fail(TDSE_EINVAL, "samples_per_step must be 1 or 2");
     if (nsteps < 0) return fail(TDSE_EINVAL, "nsteps must be >= 0");
+    if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t cb = sizeof(double2) * ctx->N;
     const size_t fb = sizeof(double) * ((size_t)samples_per_step * nsteps + 1);
@@ -498,6 +683,10 @@ tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, 
     cudaStream_t s = (cudaStream_t)stream;
     const long long N = ctx->N;
     const long S = (long)samples_per_step * nsteps + 1;
+    if (ctx->prec == TDSE_BF16X3) {
+        if (nsteps == 0) return TDSE_OK;
+        return propagate_batch_tc(ctx, c, field, B, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold, s);
+    }
     if (ctx->prec != TDSE_FP32) {
         // FP64 / float-float products: the pulses run one after the other on
         // the single-system path.
@@ -571,6 +760,7 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
     g_err.clear();
     tdse_status st = check_prop_args(ctx, c0, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold);
     if (st != TDSE_OK) return st;
+    if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
     if (!weights || !grad_field) return fail(TDSE_EINVAL, "weights and grad_field must not be NULL");
     if (checkpoint_every < 1) return fail(TDSE_EINVAL, "checkpoint_every must be >= 1");
     if (c_final && !aligned16(c_final)) return fail(TDSE_EINVAL, "c_final must be 16-byte aligned");
@@ -738,6 +928,7 @@ tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **
     for (int i = 0; i < count; ++i) {
         if (!systems[i]) return fail(TDSE_EINVAL, "systems[%d] is NULL", i);
         if (systems[i]->prec != systems[0]->prec) return fail(TDSE_EINVAL, "all systems must share one precision");
+        if (systems[i]->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
         for (int j = 0; j < i; ++j)
             if (systems[j] == systems[i]) return fail(TDSE_EINVAL, "systems[%d] repeats systems[%d]", i, j);
     }

@@ -1,0 +1,455 @@
+// Batched pulses on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// D_l = U_l X_{l+1} + U_{l-1}^T X_{l-1} (paper Sec. 4, block form of H C for
+// all pulses at once) with bf16x3 split precision: U = Uh + Ul and
+// X = Xh + Xl in bf16, and D = Uh Xh + Uh Xl + Ul Xh accumulated in FP32 in
+// tensor memory.  The transposed blocks U_l^T are stored explicitly, so both
+// products read K-major tiles.  Per CTA: one 128 x 256 output tile (128 rows
+// of block l, 128 pulses as re/im column pairs), warp 0 streams K tiles of A
+// and B with TMA into a 2-stage ring, one thread of warp 1 issues
+// tcgen05.mma, warps 2..5 read the accumulator with tcgen05.ld and apply the
+// RK4 stage / Taylor term update.  The batched state is float-float
+// (FP32 hi + lo, about 44 bits): the GB300 FP64 pipe is 1/64 of the FP32
+// pipe, and an FP64 state update would cost more than the products.
+// All waits are bounded (sync.cuh).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "sync.cuh"
+#include "tc.h"
+
+namespace tdse {
+
+constexpr int TBM = 128, TBN = 256, TBK = 64, TST = 2;
+constexpr int A_BYTES = TBM * TBK * 2;                  // 16 KB
+constexpr int B_BYTES = TBN * TBK * 2;                  // 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB
+constexpr int TC_SMEM = TST * STAGE_BYTES + 1024;       // + alignment slack
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes (64 bf16), 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)(16u >> 4) << 16;                   // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024u >> 4) << 32;                 // stride byte offset between 8-row groups
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B, both
+// K-major, M = 128, N = TBN.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// ----------------------------------------------------- float-float update --
+__device__ __forceinline__ df df_fast2sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df{s, e};
+}
+
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return df_fast2sum(p, e);
+}
+
+__device__ __forceinline__ df df_mulf(df a, float b)
+{
+    float p = __fmul_rn(a.h, b);
+    float e = __fmaf_rn(a.h, b, -p);
+    e = __fmaf_rn(a.l, b, e);
+    return df_fast2sum(p, e);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.h, -a.l}; }
+
+struct dfc { df re, im; };
+
+__device__ __forceinline__ dfc ld_dfc(const float4 *p) { float4 v = *p; return dfc{df{v.x, v.y}, df{v.z, v.w}}; }
+__device__ __forceinline__ void st_dfc(float4 *p, dfc a) { *p = make_float4(a.re.h, a.re.l, a.im.h, a.im.l); }
+__device__ __forceinline__ dfc dfc_axpy(dfc c, df s, dfc k)   // c + s k
+{
+    return dfc{df_add(c.re, df_mul(s, k.re)), df_add(c.im, df_mul(s, k.im))};
+}
+
+__device__ __forceinline__ void split_bf16(df v, __nv_bfloat16 *h, __nv_bfloat16 *l)
+{
+    const __nv_bfloat16 hb = __float2bfloat16_rn(v.h);
+    *h = hb;
+    *l = __float2bfloat16_rn(__fadd_rn(__fsub_rn(v.h, __bfloat162float(hb)), v.l));
+}
+
+// One (pulse b, amplitude a) with D x = (dr, di): RK4 stage / Taylor term.
+__device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, df e, df f, float dr, float di)
+{
+    const long long q = (long long)b * A.N + a;
+    const bool rk4 = A.mode == 2;
+    const bool from_c = rk4 ? (A.stage == 0) : (A.stage == 1);
+    const dfc xin = ld_dfc(from_c ? A.c + q : A.x + q);
+    // H x = E x + f D x ;  k = -i H x = (Im, -Re)
+    const df hr = df_add(df_mul(e, xin.re), df_mulf(f, dr));
+    const df hi = df_add(df_mul(e, xin.im), df_mulf(f, di));
+    const dfc k{hi, df_neg(hr)};
+    dfc out;
+    if (rk4) {
+        const dfc c = from_c ? xin : ld_dfc(A.c + q);
+        if (A.stage == 0) {
+            st_dfc(A.acc + q, k);
+            out = dfc_axpy(c, A.half_dt, k);
+            st_dfc(A.x + q, out);
+        } else if (A.stage < 3) {
+            const dfc ac = ld_dfc(A.acc + q);
+            const df two{2.f, 0.f};
+            st_dfc(A.acc + q, dfc{df_add(ac.re, df_mul(two, k.re)), df_add(ac.im, df_mul(two, k.im))});
+            out = dfc_axpy(c, A.stage == 1 ? A.half_dt : A.full_dt, k);
+            st_dfc(A.x + q, out);
+        } else {
+            const dfc ac = ld_dfc(A.acc + q);
+            const dfc s{df_add(ac.re, k.re), df_add(ac.im, k.im)};
+            out = dfc_axpy(c, A.sixth_dt, s);
+            st_dfc(A.c + q, out);
+        }
+    } else {
+        const dfc T{df_mul(A.term_dt, k.re), df_mul(A.term_dt, k.im)};
+        const dfc base = (A.stage == 1) ? xin : ld_dfc(A.acc + q);
+        const dfc sum{df_add(base.re, T.re), df_add(base.im, T.im)};
+        if (A.stage < A.order) {
+            st_dfc(A.acc + q, sum);
+            st_dfc(A.x + q, T);
+            out = T;
+        } else {
+            st_dfc(A.c + q, sum);
+            out = sum;
+        }
+    }
+    const int l = (int)(a / A.n);
+    const long long col = (a - (long long)l * A.n) + (long long)l * A.nb;
+    const long long pr = (2LL * b) * A.plane + col, pi = (2LL * b + 1) * A.plane + col;
+    split_bf16(out.re, A.xo_h + pr, A.xo_l + pr);
+    split_bf16(out.im, A.xo_h + pi, A.xo_l + pi);
+}
+
+// ------------------------------------------------------------------ kernel --
+// Persistent: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// Two accumulators of TBN columns live in tensor memory, so the epilogue of
+// one tile runs while the products of the next are issued.
+constexpr int EPI_WARPS = 8;                       // 2 per TMEM lane quarter
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA issuer, epilogue
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUtensorMap tmUl,
+          const __grid_constant__ CUtensorMap tmTh, const __grid_constant__ CUtensorMap tmTl,
+          const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl, TcArgs A)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[TST];
+    __shared__ __align__(8) uint64_t empty[TST];
+    __shared__ __align__(8) uint64_t acc_full[2];
+    __shared__ __align__(8) uint64_t acc_empty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int issued, consumed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = A.n;
+    const int nk = (n + TBK - 1) / TBK;
+    const int mt = (n + TBM - 1) / TBM;
+    const int nt = (2 * A.B + TBN - 1) / TBN;
+    const int ntiles = mt * nt * (A.lmax + 1);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], EPI_WARPS);
+        }
+        abort_flag = 0;
+        issued = 0;
+        consumed = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(2 * TBN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    volatile int *abort = &abort_flag;
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+                const int l = t / (mt * nt), rem = t % (mt * nt);
+                const int i0 = (rem / nt) * TBM, c0 = (rem % nt) * TBN;
+                for (int part = 0; part < 2 && !*abort; ++part) {
+                    if ((part == 0 && l >= A.lmax) || (part == 1 && l < 1)) continue;
+                    const CUtensorMap *ta_h = part == 0 ? &tmUh : &tmTh;
+                    const CUtensorMap *ta_l = part == 0 ? &tmUl : &tmTl;
+                    const int ablk = part == 0 ? l : l - 1;
+                    const int xcol = (part == 0 ? l + 1 : l - 1) * A.nb;
+                    for (int kt = 0; kt < nk; ++kt, ++it) {
+                        const int s = it % TST;
+                        if (it >= TST &&
+                            !mbar_wait_bounded(&empty[s], (uint32_t)(((it / TST) - 1) & 1), abort, TC_WAIT_NS))
+                            break;
+                        unsigned char *st = smem + (size_t)s * STAGE_BYTES;
+                        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                        tma_load_3d(st, ta_h, kt * TBK, i0, ablk, &full[s]);
+                        tma_load_3d(st + A_BYTES, ta_l, kt * TBK, i0, ablk, &full[s]);
+                        tma_load_2d(st + 2 * A_BYTES, &tmXh, xcol + kt * TBK, c0, &full[s]);
+                        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmXl, xcol + kt * TBK, c0, &full[s]);
+                        issued = it + 1;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(TBM, TBN);
+            int it = 0, j = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++j) {
+                const int l = t / (mt * nt);
+                const int T = nk * ((l < A.lmax ? 1 : 0) + (l >= 1 ? 1 : 0));
+                const int ab = j & 1;
+                if (j >= 2 && !mbar_wait_bounded(&acc_empty[ab], (uint32_t)(((j >> 1) - 1) & 1), abort, TC_WAIT_NS))
+                    break;
+                tc_fence_after();
+                const uint32_t dt_mem = tmem + (uint32_t)(ab * TBN);
+                for (int q = 0; q < T; ++q, ++it) {
+                    const int s = it % TST;
+                    if (!mbar_wait_bounded(&full[s], (uint32_t)((it / TST) & 1), abort, TC_WAIT_NS)) break;
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                    const uint64_t ah = desc_sw128(base), al = desc_sw128(base + A_BYTES);
+                    const uint64_t bh = desc_sw128(base + 2 * A_BYTES), bl = desc_sw128(base + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TBK / 16; ++kk) {
+                        const uint64_t ko = (uint64_t)((kk * 32) >> 4);   // 16 bf16 = 32 bytes along K
+                        mma_bf16(dt_mem, ah + ko, bh + ko, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(dt_mem, ah + ko, bl + ko, idesc, 1u);
+                        mma_bf16(dt_mem, al + ko, bh + ko, idesc, 1u);
+                    }
+                    mma_commit(&empty[s]);      // the stage can be refilled once these products finish
+                    consumed = it + 1;
+                }
+                mma_commit(&acc_full[ab]);      // this tile's accumulator is complete
+            }
+        }
+    } else {
+        // ------------------------------------------- epilogue: warps 2..9
+        const int quarter = warp & 3;                    // TMEM lanes this warp may read
+        const int half = (warp - 2) >> 2;                // which half of the TBN columns
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            const int l = t / (mt * nt), rem = t % (mt * nt);
+            const int i0 = (rem / nt) * TBM, c0 = (rem % nt) * TBN;
+            const int T = nk * ((l < A.lmax ? 1 : 0) + (l >= 1 ? 1 : 0));
+            const int ab = j & 1;
+            bool have = mbar_wait_bounded(&acc_full[ab], (uint32_t)((j >> 1) & 1), abort, TC_WAIT_NS);
+            have = __all_sync(0xffffffffu, have);
+            if (!have) break;
+            tc_fence_after();
+            const int row = i0 + quarter * 32 + lane;
+            const long long a = (long long)l * n + row;
+            const bool valid_row = row < n;
+            df e{0.f, 0.f};
+            if (valid_row) { const float2 ev = A.Edf[a]; e = df{ev.x, ev.y}; }
+#pragma unroll 1
+            for (int chunk = half * (TBN / 64); chunk < (half + 1) * (TBN / 64); ++chunk) {
+                float v[32];
+                if (T > 0) {
+                    tmem_ld32(tmem + (uint32_t)(ab * TBN) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(chunk * 32), v);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) v[q] = 0.f;
+                }
+                if (valid_row) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int pb = chunk * 16 + jj;        // pulse within the tile
+                        const int b = c0 / 2 + pb;
+                        if (b < A.B) {
+                            const float2 fv = A.fdf[b];
+                            tc_update(A, b, a, e, df{fv.x, fv.y}, v[2 * jj], v[2 * jj + 1]);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ab]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort) {
+        // Let copies and products still in flight finish before the CTA's
+        // shared and tensor memory go away.
+        volatile int never = 0;
+        for (int q = consumed; q < issued; ++q)
+            mbar_wait_bounded(&full[q % TST], (uint32_t)((q / TST) & 1), &never, TC_WAIT_NS);
+        atomicOr(A.err, kErrTimeout);
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
+    }
+}
+
+// Field value of every pulse at every stage time, as float-float:
+// fdf[(k*3 + h)*B + b] = f_b(t_k + h dt/2).
+__global__ void tc_field_kernel(const double *__restrict__ field, int S, int sps, long long nsteps, int B,
+                                float2 *__restrict__ fdf)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nsteps * 3 * B) return;
+    const int b = (int)(q % B);
+    const long long kh = q / B;
+    const long long k = kh / 3;
+    const int h = (int)(kh % 3);
+    const df v = df_from_double(field_at(field + (long long)b * S, sps, k, h));
+    fdf[q] = make_float2(v.h, v.l);
+}
+
+cudaError_t launch_tc_field(const double *field, int S, int sps, long long nsteps, int B, float2 *fdf,
+                            cudaStream_t stream)
+{
+    const long long tot = nsteps * 3 * B;
+    if (tot <= 0) return cudaSuccess;
+    tc_field_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(field, S, sps, nsteps, B, fdf);
+    return cudaGetLastError();
+}
+
+// FP64 [B][N] complex -> float-float state + bf16 planes; and back.
+__global__ void tc_in_kernel(const double2 *__restrict__ c, float4 *__restrict__ cdf, __nv_bfloat16 *__restrict__ xh,
+                             __nv_bfloat16 *__restrict__ xl, long long N, int n, int nb, long long plane, int B)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N * B) return;
+    const int b = (int)(q / N);
+    const long long a = q - (long long)b * N;
+    const double2 v = c[q];
+    const df r = df_from_double(v.x), i = df_from_double(v.y);
+    cdf[q] = make_float4(r.h, r.l, i.h, i.l);
+    const int l = (int)(a / n);
+    const long long col = (a - (long long)l * n) + (long long)l * nb;
+    split_bf16(r, xh + (2LL * b) * plane + col, xl + (2LL * b) * plane + col);
+    split_bf16(i, xh + (2LL * b + 1) * plane + col, xl + (2LL * b + 1) * plane + col);
+}
+
+__global__ void tc_out_kernel(const float4 *__restrict__ cdf, double2 *__restrict__ c, long long tot)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= tot) return;
+    const float4 v = cdf[q];
+    c[q] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+cudaError_t launch_tc(const TcMaps &m, const TcArgs &A, cudaStream_t stream)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    const int ntiles = ((A.n + TBM - 1) / TBM) * ((2 * A.B + TBN - 1) / TBN) * (A.lmax + 1);
+    const int grid = ntiles < sms ? ntiles : sms;
+    tc_kernel<<<grid, TC_THREADS, TC_SMEM, stream>>>(m.Uh, m.Ul, m.Th, m.Tl, m.Xh, m.Xl, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_in(const double2 *c, float4 *cdf, __nv_bfloat16 *xh, __nv_bfloat16 *xl, long long N, int n,
+                         int nb, long long plane, int B, cudaStream_t stream)
+{
+    const long long tot = N * B;
+    tc_in_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(c, cdf, xh, xl, N, n, nb, plane, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_out(const float4 *cdf, double2 *c, long long tot, cudaStream_t stream)
+{
+    tc_out_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(cdf, c, tot);
+    return cudaGetLastError();
+}
+
+}  // namespace tdse

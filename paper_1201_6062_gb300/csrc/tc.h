@@ -1,0 +1,39 @@
+// Tensor-core (tcgen05) batched propagation: arguments and launchers.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include "common.cuh"
+
+namespace tdse {
+
+// TMA descriptors: dipole planes (hi, lo), transposed dipole planes (hi, lo)
+// and the current input state planes (hi, lo).
+struct TcMaps {
+    CUtensorMap Uh, Ul, Th, Tl, Xh, Xl;
+};
+
+struct TcArgs {
+    int n, lmax, B, nb;
+    long long N;            // amplitudes per pulse
+    long long plane;        // elements per state plane: (lmax+1)*nb
+    int S, sps;             // field samples per pulse, samples per step
+    int mode, stage, order, hold;
+    long long k;
+    df half_dt, full_dt, sixth_dt, term_dt;   // dt/2, dt, dt/6 and (Taylor) dt/m as float-float
+    const float2 *Edf;      // energies as float-float [N]
+    const double *field;    // [B][S]
+    const float2 *fdf;      // this stage's field value per pulse, float-float [B]
+    float4 *c, *x, *acc;    // float-float complex states [B][N]
+    __nv_bfloat16 *xo_h, *xo_l;   // output planes [2B][plane]
+    int *err;
+};
+
+cudaError_t launch_tc(const TcMaps &m, const TcArgs &A, cudaStream_t stream);
+cudaError_t launch_tc_in(const double2 *c, float4 *cdf, __nv_bfloat16 *xh, __nv_bfloat16 *xl, long long N, int n,
+                         int nb, long long plane, int B, cudaStream_t stream);
+cudaError_t launch_tc_field(const double *field, int S, int sps, long long nsteps, int B, float2 *fdf,
+                            cudaStream_t stream);
+cudaError_t launch_tc_out(const float4 *cdf, double2 *c, long long tot, cudaStream_t stream);
+
+}  // namespace tdse

@@ -52,7 +52,7 @@ def test_host_side_argument_checks(lib):
     assert lib.tdse_create(E, None, 0, 5000, 0, ctypes.byref(out)) == 1
     assert lib.tdse_create(E, None, 2, 4, 0, ctypes.byref(out)) == 1
     assert b"dipole" in lib.tdse_last_error()
-    assert lib.tdse_create(E, None, 0, 4, 3, ctypes.byref(out)) == 5   # BF16X3 single-instance: unsupported
+    assert lib.tdse_create(E, None, 0, 4, 7, ctypes.byref(out)) == 1   # unknown precision
     assert lib.tdse_create(None, None, 0, 4, 0, ctypes.byref(out)) == 1
     assert out.value is None
     lib.tdse_propagate.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_double, ctypes.c_long] + \

@@ -70,3 +70,49 @@ def test_batched_equals_single_instance_fp32_per_pulse_within_rounding(tdse_lib)
         c = torch.from_numpy(C0[b].copy()).cuda()
         H.propagate(c, torch.from_numpy(F[b]).cuda(), dt, nsteps)
         assert rel(cb.view(B, -1)[b].cpu().numpy(), c.cpu().numpy()) < 1e-5
+
+
+# ------------------------------------------------ bf16x3 on the tensor cores --
+# bf16x3 keeps about 16 significant bits per product (the dropped lo*lo term
+# and the bf16 representation of U and X, 2^-16..2^-17), accumulated in FP32;
+# over the short windows here the amplitudes must stay within the 1e-5 target.
+
+@pytest.mark.parametrize("lmax,n,B,nsteps", [(1, 128, 4, 6), (2, 200, 7, 10), (3, 1000, 130, 8), (0, 40, 3, 5),
+                                             (2, 40, 5, 7), (4, 300, 256, 4), (1, 513, 1, 9)])
+def test_bf16x3_batched_rk4_matches_oracle(tdse_lib, lmax, n, B, nsteps):
+    dt, sps = 0.02, 1
+    E, U, F, C0 = sweep(lmax, n, B, nsteps, sps)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "bf16x3")
+    c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(c, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps)
+    H.sync()
+    got = c.cpu().numpy().reshape(B, -1)
+    for b in range(0, B, max(1, B // 9)):
+        ref, _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, nsteps)
+        assert rel(got[b], ref) < 1e-5, b
+
+
+@pytest.mark.parametrize("K,hold,sps", [(6, 0, 1), (5, 1, 2)])
+def test_bf16x3_batched_taylor_matches_oracle(tdse_lib, K, hold, sps):
+    lmax, n, B, dt, nsteps = 3, 300, 9, 0.02, 12
+    E, U, F, C0 = sweep(lmax, n, B, nsteps, sps)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "bf16x3")
+    c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(c, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps, "taylor", order=K, hold=hold,
+                      samples_per_step=sps)
+    H.sync()
+    got = c.cpu().numpy().reshape(B, -1)
+    for b in range(B):
+        ref, _ = oracle.taylor(lmax, n, E, U, C0[b], F[b], dt, nsteps, K, samples_per_step=sps, hold=hold)
+        assert rel(got[b], ref) < 1e-5, b
+
+
+def test_bf16x3_context_rejects_single_system_calls(tdse_lib):
+    E = inputs.energies(1, 64)
+    H = tdse_lib.Hamiltonian(E, inputs.dipoles(1, 64, 1), 1, 64, "bf16x3")
+    c = torch.from_numpy(inputs.ground_state(1, 64)).cuda()
+    with pytest.raises(tdse_lib.TDSEError):
+        H.propagate(c, torch.zeros(3, dtype=torch.float64, device="cuda"), 0.01, 2)
+    # populations still work on such a context
+    p = H.populations(c)
+    assert abs(p["bound"].item() - 1.0) < 1e-15
