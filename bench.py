@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound on the oracle timing sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-sweep", action="store_true", help="skip the batched pulse-sweep section")
+    p.add_argument("--sweep-pulses", type=int, default=256)
     p.add_argument("--accuracy-steps", type=int, default=2000,
                    help="steps of the error pass (the workload's 2000-step window; 0 skips it)")
     return p.parse_args()
@@ -215,6 +217,73 @@ def config_dict(cfg, variant):
             "l2": "no flush: each step streams every dipole block (496-992 MB) through the 129 MB L2"}
 
 
+def pulse_sweep_section(args):
+    """Many pulses sharing one Hamiltonian (lmax=15, n=1000; E0 log-spaced
+    0.01..0.1, omega uniform 0.3..0.9): amplitude-updates/s of the batched
+    bf16x3 tensor-core and FP32 paths next to the single-system FP64 and FP32
+    paths on the same Hamiltonian, and the batched paths' error against the
+    CPU oracle on sampled pulses over the timed window."""
+    import torch
+    import oracle
+    from paper_1201_6062_gb300 import inputs, tdse
+    cfg = inputs.pulse_sweep(args.sweep_pulses)
+    lmax, n, dt, B = cfg["lmax"], cfg["n"], cfg["dt"], cfg["B"]
+    N = (lmax + 1) * n
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, cfg["seed"])
+    W, K = 2, 10
+    t0 = 40.0                                   # inside every pulse (the shortest lasts ~70 a.u.)
+    F = np.stack([inputs.field_samples(a, w, dt, W + K, 1, t0=t0) for a, w in zip(cfg["E0"], cfg["omega"])])
+    C0 = np.tile(inputs.ground_state(lmax, n), (B, 1))
+    dev = torch.device("cuda")
+    out = {"workload": "pulse sweep lmax=15 n=1000 (16000 amplitudes) x %d pulses, RK4, dt=0.01, window "
+                       "t=40..40.12 a.u." % B}
+    sampled = [0, B // 2, B - 1]
+    refs = {}
+    for b in sampled:
+        refs[b], _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, W + K)
+    for prec in ("bf16x3", "fp32"):
+        H = tdse.Hamiltonian(E, U, lmax, n, prec)
+        c = torch.from_numpy(C0.reshape(-1).copy()).to(dev)
+        fw = torch.from_numpy(np.ascontiguousarray(F[:, :W + 1]).reshape(-1)).to(dev)
+        ft = torch.from_numpy(np.ascontiguousarray(F[:, W:]).reshape(-1)).to(dev)
+        H.propagate_batch(c, fw, B, dt, W)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        H.propagate_batch(c, ft, B, dt, K)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        got = c.cpu().numpy().reshape(B, -1)
+        err = max(float(np.linalg.norm(got[b] - refs[b]) / np.linalg.norm(refs[b])) for b in sampled)
+        flop = 4 * 2 * 2 * lmax * n * n * 2 * B * (3 if prec == "bf16x3" else 1)
+        out[prec] = {"value": N * B / (ms / 1e3), "ms_per_step": ms, "err_vs_oracle_max": err,
+                     "sampled_pulses": sampled,
+                     "tensor_or_fma_tflops": flop / (ms / 1e3) / 1e12}
+        H.close()
+        del c
+    for prec in ("fp64", "fp32"):
+        H = tdse.Hamiltonian(E, U, lmax, n, prec)
+        c = torch.from_numpy(C0[0].copy()).to(dev)
+        f = torch.from_numpy(F[0]).to(dev)
+        H.propagate(c, f[:W + 1].contiguous(), dt, W)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        H.propagate(c, f[W:].contiguous(), dt, K)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        out["single_" + prec] = {"value": N / (ms / 1e3), "ms_per_step": ms}
+        H.close()
+    out["speedup_bf16x3_vs_single_fp64"] = out["bf16x3"]["value"] / out["single_fp64"]["value"]
+    out["speedup_bf16x3_vs_single_fp32"] = out["bf16x3"]["value"] / out["single_fp32"]["value"]
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_1201_6062_gb300 import build
@@ -336,6 +405,10 @@ def run_ours(args):
                "d2h_bytes_per_step": N * 16 / K,
                "note": "tdse_propagate_host: pinned host c and field in, K steps, c out, synchronised"}
 
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = pulse_sweep_section(args)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, args.cpu_seconds, E, U)
@@ -350,6 +423,7 @@ def run_ours(args):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": p["gpu_launches"],
             "variants": res,
+            "pulse_sweep": sweep,
         }
         print(json.dumps(line))
 

@@ -1,6 +1,8 @@
-"""Profiling driver: repeated block mat-vec launches on one system, for ncu.
+"""Profiling driver for ncu: repeated block mat-vec launches on one system,
+or (with --batch B) batched RK4 steps of B pulses sharing one Hamiltonian.
 
     python -m paper_1201_6062_gb300.profile_product --prec fp32 --lmax 31 --n 2000
+    python -m paper_1201_6062_gb300.profile_product --prec bf16x3 --lmax 15 --n 1000 --batch 256
 
 Builds the library if needed, runs 5 untimed products and then `--reps`
 timed ones (CUDA events per launch via tdse_profile_*), and prints the mean
@@ -21,7 +23,8 @@ from paper_1201_6062_gb300 import build  # noqa: E402
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "df32"])
+    p.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "df32", "bf16x3"])
+    p.add_argument("--batch", type=int, default=0, help="pulses of a batched run (0: single-system products)")
     p.add_argument("--lmax", type=int, default=31)
     p.add_argument("--n", type=int, default=2000)
     p.add_argument("--seed", type=int, default=1)
@@ -29,6 +32,8 @@ def main():
     a = p.parse_args()
     build.build()
     from paper_1201_6062_gb300 import inputs, tdse
+    if a.batch:
+        return batched(a)
     E = inputs.energies(a.lmax, a.n)
     U = inputs.dipoles(a.lmax, a.n, a.seed)
     H = tdse.Hamiltonian(E, U, a.lmax, a.n, a.prec)
@@ -47,6 +52,28 @@ def main():
     alg = a.lmax * a.n * a.n * ub + (a.lmax + 1) * a.n * 32
     print("%s lmax=%d n=%d: %.4f ms per product, %.1f GB/s algorithmic (%d bytes per launch)"
           % (a.prec, a.lmax, a.n, ms / nmv, alg / (ms / nmv) / 1e6, alg))
+
+
+def batched(a):
+    import numpy as np
+    from paper_1201_6062_gb300 import inputs, tdse
+    B, dt, steps = a.batch, 0.01, 3
+    E = inputs.energies(a.lmax, a.n)
+    U = inputs.dipoles(a.lmax, a.n, a.seed)
+    H = tdse.Hamiltonian(E, U, a.lmax, a.n, a.prec)
+    cfg = inputs.pulse_sweep(B)
+    F = inputs.sweep_fields(cfg["E0"], cfg["omega"], dt, steps, 1)
+    c = torch.from_numpy(np.tile(inputs.ground_state(a.lmax, a.n), B)).cuda()
+    f = torch.from_numpy(F.reshape(-1)).cuda()
+    H.propagate_batch(c, f, B, dt, steps)          # warm-up (stages 0..11 under ncu: use -s 8 -c 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    H.propagate_batch(c, f, B, dt, steps)
+    e1.record()
+    e1.synchronize()
+    H.sync()
+    print("%s batch %d lmax=%d n=%d: %.4f ms per RK4 step" % (a.prec, B, a.lmax, a.n, e0.elapsed_time(e1) / steps))
 
 
 if __name__ == "__main__":
