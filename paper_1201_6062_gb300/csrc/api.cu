@@ -1,6 +1,7 @@
 // C ABI of the propagator (declarations and contracts in include/tdse.h).
 // Host orchestration only: argument checks, device storage, the work plan and
 // the launch sequence.  Every arithmetic step runs in the kernels.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -76,7 +77,7 @@ struct MvPlan {
 struct tdse_ctx {
     int lmax = 0, n = 0, N = 0, ld = 0, prec = 0;
     long long bstride = 0;
-    DevBuf U, E, R, P, x, acc, xq, sb, sys;
+    DevBuf U, E, R, P, x, acc, xq, sb, sys, umax;
     DevBuf part;                       // populations scratch
     DevBuf errw;                       // device status word (kErrTimeout, ...)
     DevBuf hc, hfield;                 // device copies for the host-buffer entry point
@@ -399,6 +400,18 @@ tdse_status tdse_create(const double *energies, const double *dipole_blocks, int
     }
     CTRY(c->E.ensure(sizeof(double) * c->N));
     CTRY(cudaMemcpy(c->E.p, energies, sizeof(double) * c->N, cudaMemcpyHostToDevice));
+    {
+        // per-block max |U_l|, rounded up to float
+        std::vector<float> um((size_t)(lmax > 0 ? lmax : 1), 0.f);
+        for (int l = 0; l < lmax; ++l) {
+            double m = 0.0;
+            const double *src = dipole_blocks + (size_t)l * n * n;
+            for (size_t q = 0; q < (size_t)n * n; ++q) m = std::fabs(src[q]) > m ? std::fabs(src[q]) : m;
+            um[(size_t)l] = std::nextafter((float)m, INFINITY);
+        }
+        CTRY(c->umax.ensure(sizeof(float) * um.size()));
+        CTRY(cudaMemcpy(c->umax.p, um.data(), sizeof(float) * um.size(), cudaMemcpyHostToDevice));
+    }
     tdse::Plan plan;
     st = build_plan(prec, std::vector<int>{lmax}, std::vector<int>{n}, c->plan, plan);
     if (st != TDSE_OK) return bail(st);
@@ -420,6 +433,7 @@ tdse_status tdse_create(const double *energies, const double *dipole_blocks, int
     SysDesc &d = c->desc;
     d.U = c->U.p; d.bstride = c->bstride; d.ld = c->ld; d.n = n; d.lmax = lmax; d.N = c->N;
     d.E = c->E.as<double>(); d.R = c->R.as<double2>(); d.P = c->P.as<double2>(); d.sb = c->sb.as<int>();
+    d.umax = c->umax.as<float>();
     d.c = nullptr; d.x = c->x.as<double2>(); d.acc = c->acc.as<double2>(); d.xq = c->xq.p; d.field = nullptr;
     *out = c;
     return TDSE_OK;

@@ -29,6 +29,7 @@ struct SysDesc {
     double2 *R;
     double2 *P;
     const int *sb;
+    const float *umax;      // [lmax]: max |U_l| (bounds for the float-float row sums)
     double2 *c, *x, *acc;
     void *xq;
     const double *field;
@@ -101,6 +102,7 @@ __device__ __forceinline__ double shfl_xor_d(double v, int m)
 // FP64 products: U stored as double, 2 columns per 16-byte load.
 struct PolF64 {
     static constexpr int CW = 2;
+    static constexpr bool kOffsetSums = false;   // plain accumulators
     using Elem = double;
     using Uv = double;
     using Comp = double;
@@ -129,6 +131,24 @@ struct PolF64 {
     static __device__ __forceinline__ Comp add(Comp a, Comp b) { return a + b; }
     static __device__ __forceinline__ Comp add_fast(Comp a, Comp b) { return a + b; }
     static __device__ __forceinline__ Comp shfl(Comp a, int m) { return shfl_xor_d(a, m); }
+    // Short row sums use the plain accumulator.
+    using RowAcc = Comp;
+    using Sigma = int;
+    static __device__ __forceinline__ RowAcc rzero(Sigma) { return zero(); }
+    static __device__ __forceinline__ void rfmax(RowAcc &re, RowAcc &im, Uv u, const XV &x, Sigma)
+    {
+        fmax_(re, im, u, x);
+    }
+    static __device__ __forceinline__ Comp rdone(RowAcc a, Sigma) { return a; }
+    template <int K> static __device__ __forceinline__ Sigma sigma(const XV *, float) { return 0; }
+    // Column sums: per-chunk partials folded into the running sum.
+    static __device__ __forceinline__ Sigma csigma(float, float) { return 0; }
+    static __device__ __forceinline__ float xabs(const XV &x) { return fmaxf(fabsf((float)x.re), fabsf((float)x.im)); }
+    static __device__ __forceinline__ void cfold(Comp &run, RowAcc &a, Sigma)
+    {
+        run = add(run, a);
+        a = zero();
+    }
     static __device__ __forceinline__ double to_double(Comp a) { return a; }
     static __device__ __forceinline__ void store_xq(void *xq, long long a, double2 v)
     {
@@ -139,6 +159,7 @@ struct PolF64 {
 // FP32 products: U stored as float, 4 columns per 16-byte load.
 struct PolF32 {
     static constexpr int CW = 4;
+    static constexpr bool kOffsetSums = false;
     using Elem = float;
     using Uv = float;
     using Comp = float;
@@ -168,6 +189,23 @@ struct PolF32 {
     static __device__ __forceinline__ Comp add(Comp a, Comp b) { return a + b; }
     static __device__ __forceinline__ Comp add_fast(Comp a, Comp b) { return a + b; }
     static __device__ __forceinline__ Comp shfl(Comp a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+    using RowAcc = Comp;
+    using Sigma = int;
+    static __device__ __forceinline__ RowAcc rzero(Sigma) { return zero(); }
+    static __device__ __forceinline__ void rfmax(RowAcc &re, RowAcc &im, Uv u, const XV &x, Sigma)
+    {
+        fmax_(re, im, u, x);
+    }
+    static __device__ __forceinline__ Comp rdone(RowAcc a, Sigma) { return a; }
+    template <int K> static __device__ __forceinline__ Sigma sigma(const XV *, float) { return 0; }
+    // Column sums: per-chunk partials folded into the running sum.
+    static __device__ __forceinline__ Sigma csigma(float, float) { return 0; }
+    static __device__ __forceinline__ float xabs(const XV &x) { return fmaxf(fabsf((float)x.re), fabsf((float)x.im)); }
+    static __device__ __forceinline__ void cfold(Comp &run, RowAcc &a, Sigma)
+    {
+        run = add(run, a);
+        a = zero();
+    }
     static __device__ __forceinline__ double to_double(Comp a) { return (double)a; }
     static __device__ __forceinline__ void store_xq(void *xq, long long a, double2 v)
     {
@@ -179,6 +217,7 @@ struct PolF32 {
 // 16-byte load; x as (re.hi, re.lo, im.hi, im.lo).
 struct PolDF32 {
     static constexpr int CW = 2;
+    static constexpr bool kOffsetSums = true;    // offset accumulators need bounds on |x|
     using Elem = float2;
     using Uv = df;
     using Comp = df;
@@ -206,6 +245,61 @@ struct PolDF32 {
     }
     static __device__ __forceinline__ Comp add(Comp a, Comp b) { return df_add(a, b); }
     static __device__ __forceinline__ Comp add_fast(Comp a, Comp b) { return df_add_lazy(a, b); }
+    // Short row sums (K products of |u| <= umax, |v| <= xmax): an offset
+    // accumulator.  T starts at sigma, a power of two >= 2 K umax xmax, so every
+    // partial sum keeps T within a factor two of sigma; then T' = fl(T + uh vh)
+    // changes by exactly d = T' - T (Sterbenz), and fma(uh, vh, -d) recovers
+    // the part of the product that T could not hold (to 2^-24 of ulp(T)).  The
+    // low-order terms go straight into L.  6 FP32 operations per product
+    // instead of the 12 of df_fma; the sum is (T - sigma) + L.
+    struct RowAcc { float T, L; };
+    using Sigma = float;
+    static __device__ __forceinline__ RowAcc rzero(Sigma s) { return RowAcc{s, 0.f}; }
+    static __device__ __forceinline__ void racc(RowAcc &a, df u, df v)
+    {
+        const float t = __fmaf_rn(u.h, v.h, a.T);
+        const float d = __fsub_rn(t, a.T);
+        const float r = __fmaf_rn(u.h, v.h, -d);
+        float L = __fadd_rn(a.L, r);
+        L = __fmaf_rn(u.h, v.l, L);
+        a.L = __fmaf_rn(u.l, v.h, L);
+        a.T = t;
+    }
+    static __device__ __forceinline__ void rfmax(RowAcc &re, RowAcc &im, Uv u, const XV &x, Sigma)
+    {
+        racc(re, u, x.re);
+        racc(im, u, x.im);
+    }
+    static __device__ __forceinline__ Comp rdone(RowAcc a, Sigma s) { return df{__fsub_rn(a.T, s), a.L}; }
+    // Column sums over at most K rows with |x| <= xmax: the same offset
+    // accumulator, folded into a float-float running sum after each chunk.
+    static __device__ __forceinline__ Sigma csigma(float xmax, float umax)
+    {
+        const float bound = 4.f * 8.f * umax * xmax;
+        if (!(bound > 0.f)) return 0x1p-100f;
+        int e;
+        frexpf(bound, &e);
+        return ldexpf(1.f, e > -100 ? e : -100);
+    }
+    static __device__ __forceinline__ float xabs(const XV &x) { return fmaxf(fabsf(x.re.h), fabsf(x.im.h)); }
+    static __device__ __forceinline__ void cfold(Comp &run, RowAcc &a, Sigma s)
+    {
+        run = df_add(run, df{__fsub_rn(a.T, s), a.L});
+        a = RowAcc{s, 0.f};
+    }
+    // sigma for K products with this thread's x values (xs[K/CW*..] flattened) and |U| <= umax
+    template <int K> static __device__ __forceinline__ Sigma sigma(const XV *xs, float umax)
+    {
+        float m = 0.f;
+#pragma unroll
+        for (int q = 0; q < K; ++q) m = fmaxf(m, fmaxf(fabsf(xs[q].re.h), fabsf(xs[q].im.h)));
+        // bound on |partial sum| with a factor 2 for the lo words and rounding, doubled again
+        const float bound = 4.f * (float)K * umax * m;
+        if (!(bound > 0.f)) return 0x1p-100f;
+        int e;
+        frexpf(bound, &e);                     // bound < 2^e
+        return ldexpf(1.f, e > -100 ? e : -100);
+    }
     static __device__ __forceinline__ Comp shfl(Comp a, int m)
     {
         return df{__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};

@@ -45,6 +45,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
     __shared__ Comp red[2][NW][V];
     __shared__ int abort_flag;
     __shared__ int issued, consumed;
+    __shared__ float xmax_sh[NW];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -122,6 +123,27 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     car[g][c] = P::zero();
                     cai[g][c] = P::zero();
                 }
+            const float um = S.umax ? S.umax[sg.l] : 0.f;
+            const typename P::Sigma sig = P::template sigma<MAXG * CW>(&xc[0][0], um);
+            // bound on |x_l| over the segment's rows, for the column sums
+            float xm = 0.f;
+            if constexpr (P::kOffsetSums) {
+                for (int r = sg.i0 + tid; r < sg.i1; r += CT) xm = fmaxf(xm, P::xabs(P::loadx(S.xq, base_l + r)));
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, off));
+                if (lane == 0) xmax_sh[warp] = xm;
+                named_sync(1, CT);
+                xm = 0.f;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) xm = fmaxf(xm, xmax_sh[w]);
+                named_sync(1, CT);
+            }
+            const typename P::Sigma csig = P::csigma(xm, um);
+            typename P::RowAcc cpr[MAXG][CW], cpi[MAXG][CW];
+#pragma unroll
+            for (int g = 0; g < MAXG; ++g)
+#pragma unroll
+                for (int c = 0; c < CW; ++c) { cpr[g][c] = P::rzero(csig); cpi[g][c] = P::rzero(csig); }
             for (int rb = sg.i0; rb < sg.i1; rb += RBT) {
                 // One ring stage (RS rows) per iteration; the stage body is unrolled
                 // but the stage loop is not, which keeps the code in the
@@ -134,9 +156,9 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     if (row0 >= sg.i1) break;
                     const int nr = min(RS, sg.i1 - row0);
                     const int s = q % NS;
-                    Comp rre[RS], rim[RS];
+                    typename P::RowAcc rre[RS], rim[RS];
 #pragma unroll
-                    for (int rr = 0; rr < RS; ++rr) { rre[rr] = P::zero(); rim[rr] = P::zero(); }
+                    for (int rr = 0; rr < RS; ++rr) { rre[rr] = P::rzero(sig); rim[rr] = P::rzero(sig); }
                     const bool live = mbar_wait_bounded(&full[s], (uint32_t)((q / NS) & 1), abort, WAIT_NS);
                     if (live) {
                         const Elem *st_rows = reinterpret_cast<const Elem *>(ring + (size_t)s * STAGE_MAX);
@@ -162,8 +184,8 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                             for (int g = 0; g < MAXG; ++g)
 #pragma unroll
                                 for (int c = 0; c < CW; ++c) {
-                                    P::fmax_(rre[rr], rim[rr], u[rr][g][c], xc[g][c]);
-                                    P::fmax_(car[g][c], cai[g][c], u[rr][g][c], xi[rr]);
+                                    P::rfmax(rre[rr], rim[rr], u[rr][g][c], xc[g][c], sig);
+                                    P::rfmax(cpr[g][c], cpi[g][c], u[rr][g][c], xi[rr], csig);
                                 }
                     }
                     __syncwarp();
@@ -172,7 +194,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     // warp transpose-reduce of the stage's 2*RS row components
                     Comp v[VS];
 #pragma unroll
-                    for (int rr = 0; rr < RS; ++rr) { v[2 * rr] = rre[rr]; v[2 * rr + 1] = rim[rr]; }
+                    for (int rr = 0; rr < RS; ++rr) { v[2 * rr] = P::rdone(rre[rr], sig); v[2 * rr + 1] = P::rdone(rim[rr], sig); }
                     int idx = 0;
 #pragma unroll
                     for (int step = 0; step < 5; ++step) {
@@ -194,6 +216,15 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     }
                     if ((lane & (DUPS - 1)) == 0) red[parity][warp][st * VS + idx] = v[0];
                 }
+                if constexpr (P::kOffsetSums) {
+#pragma unroll
+                    for (int g = 0; g < MAXG; ++g)
+#pragma unroll
+                        for (int c = 0; c < CW; ++c) {
+                            P::cfold(car[g][c], cpr[g][c], csig);
+                            P::cfold(cai[g][c], cpi[g][c], csig);
+                        }
+                }
                 named_sync(1, CT);
                 if (warp == 0 && lane < V) {
                     const int i = rb + (lane >> 1);
@@ -206,6 +237,15 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     }
                 }
                 parity ^= 1;
+            }
+            if constexpr (!P::kOffsetSums) {
+#pragma unroll
+                for (int g = 0; g < MAXG; ++g)
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) {
+                        P::cfold(car[g][c], cpr[g][c], csig);
+                        P::cfold(cai[g][c], cpi[g][c], csig);
+                    }
             }
             if (!*abort) {
                 double2 *Pslot = S.P + (long long)sg.slot * n;
