@@ -17,6 +17,10 @@ struct MvCfg {
     int RS = 0;         // rows per ring stage (tma only)
 };
 
+// Launch with programmatic stream serialization (the kernel calls pdl_wait()
+// before reading what earlier kernels wrote).
+cudaError_t launch_pdl(const void *fn, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, void **args);
+
 // prec: 0 FP64, 1 FP32, 2 DF32 (tdse_precision values).
 bool mv_config(int prec, int n, MvCfg *out);
 int mv_ctas_per_sm(int prec, const MvCfg &cfg);

@@ -16,6 +16,8 @@
 // bitwise reproducible (no atomics).  FP64 state; dipole products in the
 // arithmetic of the precision policy (common.cuh).
 #include "kernels.h"
+#include "epi.cuh"
+#include "sync.cuh"
 
 namespace tdse {
 
@@ -44,6 +46,8 @@ mv_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const i
     const int lane = tid & 31;
     int parity = 0;
 
+    pdl_launch_dependents();
+    pdl_wait();
     const int s0 = cta_off[blockIdx.x], s1 = cta_off[blockIdx.x + 1];
     for (int si = s0; si < s1; ++si) {
         const Seg sg = segs[si];
@@ -248,7 +252,7 @@ cudaError_t launch_mv(int prec, const MvCfg &cfg, int grid, const SysDesc *sys, 
     if (!fn) return cudaErrorInvalidValue;
     if (grid <= 0) return cudaSuccess;
     void *args[] = {(void *)&sys, (void *)&segs, (void *)&cta_off};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(cfg.BT), args, 0, stream);
+    return launch_pdl(fn, dim3(grid), dim3(cfg.BT), 0, stream, args);
 }
 
 // ----------------------------------------------------------- epilogue --
@@ -259,92 +263,22 @@ template <class P>
 __global__ void __launch_bounds__(256)
 epi_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, EpiArgs A)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const int2 bm = blk[blockIdx.x];
     const SysDesc &S = sys[bm.x];
     const long long a = (long long)bm.y + threadIdx.x;
     if (a >= S.N) return;
     if (A.kdev) A.k = *A.kdev;
-    const int n = S.n;
-    const int m = (int)(a / n), i = (int)(a - (long long)m * n);
-    double dr = 0.0, di = 0.0;
-    if (m < S.lmax) { const double2 r = S.R[a]; dr = r.x; di = r.y; }
-    if (m >= 1) {
-        const int b0 = S.sb[m - 1], b1 = S.sb[m];
-        for (int s = b0; s < b1; ++s) { const double2 p = S.P[(long long)s * n + i]; dr += p.x; di += p.y; }
-    }
-    const double e = S.E[a];
-    double f;
-    double2 xin;
-    if (A.mode == EPI_RK4) {
-        const int h = (A.stage == 0) ? 0 : (A.stage == 3 ? 2 : 1);
-        f = field_at(S.field, A.sps, A.k, h);
-        xin = (A.stage == 0) ? S.c[a] : S.x[a];
-    } else if (A.mode == EPI_TAYLOR) {
-        f = field_at(S.field, A.sps, A.k, A.hold ? 1 : 0);
-        xin = (A.stage == 1) ? S.c[a] : S.x[a];
-    } else {
-        f = A.fval;
-        xin = S.x[a];
-    }
-    const double hr = e * xin.x + f * dr;
-    const double hi = e * xin.y + f * di;
-    // k = -i (hr + i hi)
-    const double kr = hi, ki = -hr;
-    if (A.mode == EPI_HX) { S.acc[a] = make_double2(hr, hi); return; }
-    if (A.mode == EPI_MIHX) { S.acc[a] = make_double2(kr, ki); return; }
-    if (A.mode == EPI_RK4) {
-        const double2 c = S.c[a];
-        const double dt = A.dt;
-        if (A.stage == 0) {
-            S.acc[a] = make_double2(kr, ki);
-            const double2 xn = make_double2(c.x + 0.5 * dt * kr, c.y + 0.5 * dt * ki);
-            S.x[a] = xn;
-            P::store_xq(S.xq, a, xn);
-            if (A.st_x) A.st_x[a] = xn;
-        } else if (A.stage < 3) {
-            const double2 ac = S.acc[a];
-            S.acc[a] = make_double2(ac.x + 2.0 * kr, ac.y + 2.0 * ki);
-            const double s = (A.stage == 1) ? 0.5 * dt : dt;
-            const double2 xn = make_double2(c.x + s * kr, c.y + s * ki);
-            S.x[a] = xn;
-            P::store_xq(S.xq, a, xn);
-            if (A.st_x) A.st_x[a] = xn;
-        } else {
-            const double2 ac = S.acc[a];
-            const double w = dt / 6.0;
-            const double2 cn = make_double2(c.x + w * (ac.x + kr), c.y + w * (ac.y + ki));
-            S.c[a] = cn;
-            P::store_xq(S.xq, a, cn);
-            if (A.st_c) A.st_c[a] = cn;
-        }
-        return;
-    }
-    // Taylor term m = A.stage: T_m = (dt/m) k; sum += T_m.
-    const double s = A.dt / (double)A.stage;
-    const double2 T = make_double2(s * kr, s * ki);
-    double2 sum;
-    if (A.stage == 1) {
-        sum = make_double2(xin.x + T.x, xin.y + T.y);
-    } else {
-        const double2 ac = S.acc[a];
-        sum = make_double2(ac.x + T.x, ac.y + T.y);
-    }
-    if (A.stage < A.order) {
-        S.acc[a] = sum;
-        S.x[a] = T;
-        P::store_xq(S.xq, a, T);
-        if (A.st_x) A.st_x[a] = T;
-    } else {
-        S.c[a] = sum;
-        P::store_xq(S.xq, a, sum);
-        if (A.st_c) A.st_c[a] = sum;
-    }
+    epi_amp<P, false>(S, a, A);
 }
 
 template <class P>
 __global__ void __launch_bounds__(256)
 prep_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, int from_x)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     const int2 bm = blk[blockIdx.x];
     const SysDesc &S = sys[bm.x];
     const long long a = (long long)bm.y + threadIdx.x;
@@ -352,16 +286,33 @@ prep_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, int f
     P::store_xq(S.xq, a, from_x ? S.x[a] : S.c[a]);
 }
 
+cudaError_t launch_pdl(const void *fn, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, void **args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 cudaError_t launch_epi(int prec, int nblk, const int2 *blk, const SysDesc *sys, EpiArgs a, cudaStream_t stream)
 {
     if (nblk <= 0) return cudaSuccess;
+    const void *fn = nullptr;
     switch (prec) {
-    case 0: epi_kernel<PolF64><<<nblk, 256, 0, stream>>>(sys, blk, a); break;
-    case 1: epi_kernel<PolF32><<<nblk, 256, 0, stream>>>(sys, blk, a); break;
-    case 2: epi_kernel<PolDF32><<<nblk, 256, 0, stream>>>(sys, blk, a); break;
+    case 0: fn = (const void *)epi_kernel<PolF64>; break;
+    case 1: fn = (const void *)epi_kernel<PolF32>; break;
+    case 2: fn = (const void *)epi_kernel<PolDF32>; break;
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    void *args[] = {(void *)&sys, (void *)&blk, (void *)&a};
+    return launch_pdl(fn, dim3(nblk), dim3(256), 0, stream, args);
 }
 
 __global__ void bump_kernel(long long *kdev) { *kdev += 1; }
@@ -375,13 +326,15 @@ cudaError_t launch_bump(long long *kdev, cudaStream_t stream)
 cudaError_t launch_prep(int prec, int nblk, const int2 *blk, const SysDesc *sys, int from_x, cudaStream_t stream)
 {
     if (nblk <= 0) return cudaSuccess;
+    const void *fn = nullptr;
     switch (prec) {
-    case 0: prep_kernel<PolF64><<<nblk, 256, 0, stream>>>(sys, blk, from_x); break;
-    case 1: prep_kernel<PolF32><<<nblk, 256, 0, stream>>>(sys, blk, from_x); break;
-    case 2: prep_kernel<PolDF32><<<nblk, 256, 0, stream>>>(sys, blk, from_x); break;
+    case 0: fn = (const void *)prep_kernel<PolF64>; break;
+    case 1: fn = (const void *)prep_kernel<PolF32>; break;
+    case 2: fn = (const void *)prep_kernel<PolDF32>; break;
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    void *args[] = {(void *)&sys, (void *)&blk, (void *)&from_x};
+    return launch_pdl(fn, dim3(nblk), dim3(256), 0, stream, args);
 }
 
 }  // namespace tdse

@@ -60,6 +60,8 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_launch_dependents();
+    pdl_wait();                            // inputs (x) come from the previous kernel
     volatile int *abort = &abort_flag;
     const int s0 = cta_off[blockIdx.x], s1 = cta_off[blockIdx.x + 1];
 
@@ -361,7 +363,7 @@ cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys,
         attr_done[prec][cfg.idx][cfg.RS] = true;
     }
     void *args[] = {(void *)&sys, (void *)&segs, (void *)&cta_off, (void *)&err};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(cfg.BT), args, (size_t)smem, stream);
+    return launch_pdl(fn, dim3(grid), dim3(cfg.BT), (size_t)smem, stream, args);
 }
 
 }  // namespace tdse

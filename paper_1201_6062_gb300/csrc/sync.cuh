@@ -101,6 +101,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Programmatic dependent launch: let the next kernel in the stream start its
+// launch now, and wait until the previous kernel's results are visible.
+__device__ __forceinline__ void pdl_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Named barrier among the first `nthreads` threads (multiple of 32).
 __device__ __forceinline__ void named_sync(int id, int nthreads)
 {
