@@ -11,6 +11,7 @@ Functions follow the paper (Ó Broin & Nikolopoulos, arXiv:1201.6062):
   rk4                 App. B, Eqs. "RKFinal"/"RKDeriv", classic tableau
   taylor              App. B, Eq. "taylor" (recursion read as T_m = dt/m M T_{m-1})
   populations         Sec. 5 (continuum population = ionisation), Sec. 5.1 (unitarity)
+  lanczos             short-iterative Lanczos (the method Sec. 5.2 proposes next)
   adjoint             discrete adjoint of rk4 / taylor (the paper has no adjoint;
                       pinned by finite differences and a forward-mode tangent)
 """
@@ -53,6 +54,10 @@ def _load():
         lib.orc_rk4.restype = L
         lib.orc_taylor.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I]
         lib.orc_taylor.restype = L
+        lib.orc_lanczos.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I]
+        lib.orc_lanczos.restype = L
+        lib.orc_tridiag_eig.argtypes = [I, _dp, _dp, _dp]
+        lib.orc_tridiag_eig.restype = I
         lib.orc_populations.argtypes = [I, I, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         lib.orc_adjoint.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I, I, _dp, _dp, _dp]
         _lib = lib
@@ -139,6 +144,30 @@ def taylor(lmax, n, E, U, c0, F, dt, nsteps, order, samples_per_step=1, hold=0):
     nmv = _load().orc_taylor(lmax, n, _p(E), _p(U), _p(cv), _p(F), samples_per_step, float(dt),
                              int(nsteps), int(order), int(hold))
     return c, nmv
+
+
+def lanczos(lmax, n, E, U, c0, F, dt, nsteps, m, samples_per_step=1, hold=1):
+    """Short-iterative Lanczos propagation with m products per step; returns (c, matvecs)."""
+    E, U = _dims(E, U, lmax, n)
+    F = _check_field(F, samples_per_step, nsteps)
+    c, cv = _cvec(c0)
+    r = _load().orc_lanczos(lmax, n, _p(E), _p(U), _p(cv), _p(F), samples_per_step, float(dt), int(nsteps),
+                            int(m), int(hold))
+    if r < 0:
+        raise RuntimeError("tridiagonal eigensolver did not converge in %d steps" % (-r))
+    return c, r
+
+
+def tridiag_eig(d, e):
+    """Eigenvalues and eigenvectors (columns) of the symmetric tridiagonal (d, e)."""
+    d = _f64(d).copy()
+    m = d.size
+    ee = np.zeros(m)
+    ee[: m - 1] = _f64(e)[: m - 1]
+    z = np.zeros((m, m))
+    if _load().orc_tridiag_eig(m, _p(d), _p(ee), _p(z)) != 0:
+        raise RuntimeError("no convergence")
+    return d, z
 
 
 def populations(lmax, n, E, c):

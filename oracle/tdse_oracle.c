@@ -25,12 +25,16 @@
  *       a half step is the mean of its two neighbours.
  *   samples_per_step = 2: F[h] = f(t0 + h*dt/2), h = 0..2*nsteps.
  *
+ * Lanczos (short-iterative Lanczos, the method Sec. 5.2 proposes next)
+ * completes the set of propagators.
+ *
  * Parity pins (tests/test_oracle_pins.py): brute-force dense H on tiny
  * sizes, the closed-form field-free evolution of each scheme, the two-level
  * Rabi flop, scipy expm / solve_ivp references, RK4 == Taylor-4 for constant
  * H, convergence orders, central finite differences and a forward-mode
  * tangent for the adjoint.
  */
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -381,4 +385,137 @@ void orc_adjoint(int lmax, int n, const double *E, const double *U, double *c,
     memcpy(c, cT, sizeof(double) * 2 * N);
     *loss = L;
     free(states); free(stg); free(work); free(G); free(gc); free(gk); free(gx); free(u);
+}
+
+/*
+ * Eigen-decomposition of a real symmetric tridiagonal matrix (diagonal d[m],
+ * off-diagonal e[m], e[0..m-2] used) by the implicit QL iteration with Wilkinson shifts.
+ * On return d holds the eigenvalues and z (m x m, row-major, z[i*m+k] = component i of
+ * eigenvector k) the orthonormal eigenvectors.  Returns 0, or -1 if an eigenvalue needs
+ * more than 60 iterations.
+ */
+int orc_tridiag_eig(int m, double *d, double *e, double *z)
+{
+    for (int i = 0; i < m; ++i)
+        for (int k = 0; k < m; ++k) z[i * m + k] = (i == k) ? 1.0 : 0.0;
+    if (m > 0) e[m - 1] = 0.0;
+    for (int l = 0; l < m; ++l) {
+        int iter = 0, mm;
+        do {
+            for (mm = l; mm < m - 1; ++mm) {
+                const double dd = fabs(d[mm]) + fabs(d[mm + 1]);
+                if (fabs(e[mm]) <= 1e-16 * dd) break;
+            }
+            if (mm != l) {
+                if (++iter > 60) return -1;
+                double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+                double r = hypot(g, 1.0);
+                g = d[mm] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
+                double s = 1.0, c = 1.0, p = 0.0;
+                int i;
+                for (i = mm - 1; i >= l; --i) {
+                    double f = s * e[i], b = c * e[i];
+                    r = hypot(f, g);
+                    e[i + 1] = r;
+                    if (r == 0.0) { d[i + 1] -= p; e[mm] = 0.0; break; }
+                    s = f / r;
+                    c = g / r;
+                    g = d[i + 1] - p;
+                    r = (d[i] - g) * s + 2.0 * c * b;
+                    p = s * r;
+                    d[i + 1] = g + p;
+                    g = c * r - b;
+                    for (int k = 0; k < m; ++k) {
+                        f = z[k * m + i + 1];
+                        z[k * m + i + 1] = s * z[k * m + i] + c * f;
+                        z[k * m + i] = c * z[k * m + i] - s * f;
+                    }
+                }
+                if (r == 0.0 && i >= l) continue;
+                d[l] -= p;
+                e[l] = g;
+                e[mm] = 0.0;
+            }
+        } while (mm != l);
+    }
+    return 0;
+}
+
+/*
+ * Short-iterative Lanczos step (the Arnoldi/Lanczos propagator the paper names as the
+ * next method in Sec. 5.2; standard three-term recurrence for a Hermitian H frozen
+ * over the step):
+ *   v_0 = c / b_0, b_0 = |c|;  w = H v_j;  a_j = Re<v_j, w>;
+ *   w -= a_j v_j + b_j v_{j-1};  b_{j+1} = |w|;  v_{j+1} = w / b_{j+1}   (j < m)
+ *   T = tridiag(b, a, b);  c(t + dt) = b_0 V exp(-i T dt) e_1.
+ * A vanishing b_{j+1} (invariant subspace) ends the recurrence early.
+ */
+static int lanczos_step(int lmax, int n, const double *E, const double *U, double *c, double f, double dt, int m,
+                        double *V, double *w)
+{
+    const long N = (long)(lmax + 1) * n;
+    double b0 = 0.0;
+    for (long q = 0; q < 2 * N; ++q) b0 += c[q] * c[q];
+    b0 = sqrt(b0);
+    if (b0 == 0.0) return 0;
+    double *al = (double *)calloc((size_t)m, sizeof(double));
+    double *be = (double *)calloc((size_t)m + 1, sizeof(double));
+    for (long q = 0; q < 2 * N; ++q) V[q] = c[q] / b0;
+    int mm = m;
+    for (int j = 0; j < m; ++j) {
+        double *vj = V + (long)j * 2 * N;
+        orc_hmatvec(lmax, n, E, U, f, vj, w);
+        double a = 0.0;
+        for (long q = 0; q < 2 * N; ++q) a += vj[q] * w[q];     /* Re<v, w> */
+        al[j] = a;
+        for (long q = 0; q < 2 * N; ++q) {
+            w[q] -= a * vj[q];
+            if (j > 0) w[q] -= be[j] * V[(long)(j - 1) * 2 * N + q];
+        }
+        if (j == m - 1) break;
+        double b = 0.0;
+        for (long q = 0; q < 2 * N; ++q) b += w[q] * w[q];
+        b = sqrt(b);
+        be[j + 1] = b;
+        if (b <= 1e-300) { mm = j + 1; break; }
+        for (long q = 0; q < 2 * N; ++q) V[(long)(j + 1) * 2 * N + q] = w[q] / b;
+    }
+    double *d = (double *)malloc(sizeof(double) * mm), *e = (double *)malloc(sizeof(double) * mm);
+    double *z = (double *)malloc(sizeof(double) * mm * mm);
+    for (int j = 0; j < mm; ++j) { d[j] = al[j]; e[j] = (j + 1 < mm) ? be[j + 1] : 0.0; }
+    const int ok = orc_tridiag_eig(mm, d, e, z);
+    /* y = Q exp(-i Lambda dt) Q^T e_1 */
+    double *yr = (double *)calloc((size_t)mm, sizeof(double)), *yi = (double *)calloc((size_t)mm, sizeof(double));
+    for (int k = 0; k < mm; ++k) {
+        const double q0 = z[0 * mm + k];
+        const double cr = cos(d[k] * dt), ci = -sin(d[k] * dt);
+        for (int j = 0; j < mm; ++j) { yr[j] += z[j * mm + k] * cr * q0; yi[j] += z[j * mm + k] * ci * q0; }
+    }
+    for (long q = 0; q < N; ++q) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < mm; ++j) {
+            const double vr = V[(long)j * 2 * N + 2 * q], vi = V[(long)j * 2 * N + 2 * q + 1];
+            re += yr[j] * vr - yi[j] * vi;
+            im += yr[j] * vi + yi[j] * vr;
+        }
+        c[2 * q] = b0 * re;
+        c[2 * q + 1] = b0 * im;
+    }
+    free(al); free(be); free(d); free(e); free(z); free(yr); free(yi);
+    return ok;
+}
+
+/* Lanczos propagation, H frozen at t_k (hold 0) or t_k + dt/2 (hold 1); m products per step. */
+long orc_lanczos(int lmax, int n, const double *E, const double *U, double *c, const double *F, int sps, double dt,
+                 long nsteps, int m, int hold)
+{
+    const long N = (long)(lmax + 1) * n;
+    double *V = (double *)malloc(sizeof(double) * 2 * N * (m + 1));
+    double *w = (double *)malloc(sizeof(double) * 2 * N);
+    long bad = 0;
+    for (long k = 0; k < nsteps; ++k)
+        if (lanczos_step(lmax, n, E, U, c, orc_field_at(F, sps, k, hold ? 1 : 0), dt, m, V, w) != 0) ++bad;
+    free(V);
+    free(w);
+    return bad ? -bad : (long)m * nsteps;
 }

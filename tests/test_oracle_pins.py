@@ -344,3 +344,64 @@ def test_equal_matvec_counts_of_the_paper():
         else:
             continue   # RKF 4(5) is not implemented (no tableau in the paper)
         assert abs(nmv / (nsteps * r["dt"]) - g["equal_matvec_comparison"]["matvecs_per_au"]) < 1e-9
+
+
+# -------------------------------------------------------------- Lanczos --
+
+@pytest.mark.parametrize("m", [1, 2, 3, 7, 16, 32])
+def test_tridiagonal_eigensolver_matches_numpy(m):
+    rng = np.random.default_rng(m)
+    d = rng.standard_normal(m)
+    e = rng.standard_normal(max(m - 1, 0))
+    if m > 4:
+        e[2] = 0.0                        # a split into independent blocks
+    w, z = oracle.tridiag_eig(d, e)
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    assert np.allclose(np.sort(w), np.linalg.eigvalsh(T), atol=1e-13, rtol=0)
+    assert np.max(np.abs(T @ z - z * w)) < 1e-13
+    assert np.max(np.abs(z.T @ z - np.eye(m))) < 1e-13
+
+
+def test_lanczos_full_krylov_space_is_the_exact_exponential():
+    """With m = N the Krylov space is the whole space: each step is exp(-i H dt)."""
+    lmax, n, f, dt, nsteps = 2, 3, 0.4, 0.3, 5
+    E, U = rand_system(lmax, n, 61)
+    N = (lmax + 1) * n
+    c0 = inputs.random_state(N, 62)
+    H = np.diag(E) + f * dense_D(lmax, n, U)
+    ref = np.linalg.matrix_power(scipy.linalg.expm(-1j * H * dt), nsteps) @ c0
+    c, nmv = oracle.lanczos(lmax, n, E, U, c0, np.full(nsteps + 1, f), dt, nsteps, N)
+    assert nmv == N * nsteps
+    assert rel(c, ref) < 1e-12
+
+
+def test_lanczos_converges_in_the_krylov_dimension_and_keeps_the_norm():
+    lmax, n, f, dt, nsteps = 4, 20, 0.3, 0.2, 20
+    E, U = rand_system(lmax, n, 63)
+    N = (lmax + 1) * n
+    c0 = inputs.random_state(N, 64)
+    H = np.diag(E) + f * dense_D(lmax, n, U)
+    ref = np.linalg.matrix_power(scipy.linalg.expm(-1j * H * dt), nsteps) @ c0
+    errs = []
+    for m in (3, 5, 8, 12):
+        c, _ = oracle.lanczos(lmax, n, E, U, c0, np.full(nsteps + 1, f), dt, nsteps, m)
+        errs.append(rel(c, ref))
+        assert abs(np.linalg.norm(c) - 1.0) < 1e-13      # exp(-iT dt) of a real symmetric T is unitary
+    assert errs[0] > errs[1] > errs[2] > errs[3] and errs[3] < 1e-11, errs
+
+
+def test_lanczos_mid_hold_is_second_order_in_time():
+    lmax, n, E0, om = 2, 4, 0.8, 1.3
+    E, U = rand_system(lmax, n, 21)
+    E = E * 0.5
+    c0 = inputs.random_state((lmax + 1) * n, 22)
+    T = inputs.pulse_duration(om, cycles=2)
+    ref = _ivp_reference(lmax, n, E, U, c0, E0, om, T)
+    errs = []
+    for nsteps in (200, 400, 800):
+        dt = T / nsteps
+        F2 = inputs.field_samples(E0, om, dt, nsteps, 2, cycles=2)
+        c, _ = oracle.lanczos(lmax, n, E, U, c0, F2, dt, nsteps, 10, samples_per_step=2, hold=1)
+        errs.append(rel(c, ref))
+    r = errs[1] / errs[2]
+    assert abs(r / 4.0 - 1) < 0.1, errs
