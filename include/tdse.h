@@ -48,7 +48,12 @@ typedef enum {
 
 typedef enum {
     TDSE_RK4 = 0,       /* classic 4-stage Runge-Kutta (App. B, "RKFinal"/"RKDeriv") */
-    TDSE_TAYLOR = 1     /* truncated Taylor series (App. B, Eq. "taylor")             */
+    TDSE_TAYLOR = 1,    /* truncated Taylor series (App. B, Eq. "taylor")             */
+    TDSE_LANCZOS = 2    /* short-iterative Lanczos, the method Sec. 5.2 proposes next:
+                           `taylor_order` = Krylov dimension m (1..32) products per
+                           step, H frozen at the time `taylor_hold` selects, then
+                           c <- |c| V exp(-i T dt) e_1 with T the Lanczos tridiagonal.
+                           tdse_propagate / tdse_propagate_host only.              */
 } tdse_scheme;
 
 typedef enum {

@@ -17,6 +17,7 @@
 #include "batch.h"
 #include "plan.h"
 #include "tc.h"
+#include "lanczos.h"
 
 using tdse::SysDesc;
 using tdse::Seg;
@@ -85,6 +86,8 @@ struct tdse_ctx {
     DevBuf ac, ckpt, store, aG, ag, agc, axq, dots, lparts;
     // batched pulses: FP64 stage inputs / accumulators and the double-buffered product inputs
     DevBuf bx, bacc, bq;
+    // Lanczos: Krylov vectors, work vector, partial sums, scalars
+    DevBuf lzV, lzw, lzparts, lzscal;
     // bf16x3 tensor-core path: dipole planes, energies as float-float, float-float
     // states, double-buffered bf16 state planes and their TMA descriptors
     DevBuf tU, tEdf, tc_c, tc_x, tc_acc, tc_planes, tc_fdf;
@@ -532,10 +535,51 @@ static tdse_status check_prop_args(tdse_ctx *ctx, const double *c, const double 
     if (sps != 1 && sps != 2) return fail(TDSE_EINVAL, "samples_per_step must be 1 or 2 (got %d)", sps);
     if (!(dt == dt) || dt == 0.0 || dt > 1e300 || dt < -1e300) return fail(TDSE_EINVAL, "dt must be finite and nonzero");
     if (nsteps < 0) return fail(TDSE_EINVAL, "nsteps must be >= 0");
-    if (scheme != TDSE_RK4 && scheme != TDSE_TAYLOR) return fail(TDSE_EINVAL, "unknown scheme %d", (int)scheme);
+    if (scheme != TDSE_RK4 && scheme != TDSE_TAYLOR && scheme != TDSE_LANCZOS)
+        return fail(TDSE_EINVAL, "unknown scheme %d", (int)scheme);
     if (scheme == TDSE_TAYLOR && (order < 1 || order > 64)) return fail(TDSE_EINVAL, "taylor_order must be in 1..64");
-    if (scheme == TDSE_TAYLOR && hold != TDSE_HOLD_LEFT && hold != TDSE_HOLD_MID)
+    if (scheme == TDSE_LANCZOS && (order < 1 || order > tdse::LZ_MAX_M))
+        return fail(TDSE_EINVAL, "the Krylov dimension (taylor_order) must be in 1..%d", tdse::LZ_MAX_M);
+    if (scheme != TDSE_RK4 && hold != TDSE_HOLD_LEFT && hold != TDSE_HOLD_MID)
         return fail(TDSE_EINVAL, "unknown taylor_hold %d", hold);
+    return TDSE_OK;
+}
+
+static tdse_status propagate_lanczos(tdse_ctx *ctx, double *c, int sps, double dt, long nsteps, int m, int hold,
+                                     cudaStream_t s)
+{
+    const long long N = ctx->N;
+    const size_t vb = sizeof(double2) * (size_t)N;
+    const int nblk = (int)((N + 255) / 256);
+    CUDA_TRY(ctx->lzV.ensure(vb * (size_t)(m + 1)));
+    CUDA_TRY(ctx->lzw.ensure(vb));
+    CUDA_TRY(ctx->lzparts.ensure(sizeof(double) * 2 * (size_t)nblk));
+    CUDA_TRY(ctx->lzscal.ensure(sizeof(double) * tdse::LZ_SCAL));
+    const SysDesc *sys = ctx->sys.as<SysDesc>();
+    double2 *V = ctx->lzV.as<double2>(), *w = ctx->lzw.as<double2>();
+    double *pa = ctx->lzparts.as<double>(), *pb = pa + nblk, *scal = ctx->lzscal.as<double>();
+    tdse::LzArgs A{sps, hold, 0};
+    for (long k = 0; k < nsteps; ++k) {
+        A.k = k;
+        CUDA_TRY(tdse::lz_launch_norm(sys, N, (const double2 *)c, pa, s));
+        CUDA_TRY(tdse::lz_launch_init(ctx->prec, sys, N, (const double2 *)c, pa, V, scal, s));
+        ctx->launches += 2;
+        for (int j = 0; j < m; ++j) {
+            double2 *vj = V + (size_t)j * N;
+            tdse_status st = launch_product(ctx, 0, s);
+            if (st != TDSE_OK) return st;
+            CUDA_TRY(tdse::lz_launch_apply(sys, N, vj, w, A, pa, s));
+            CUDA_TRY(tdse::lz_launch_orth(sys, N, vj, j > 0 ? vj - N : vj, w, j, pa, scal, pb, s));
+            ctx->launches += 2;
+            if (j + 1 < m) {
+                CUDA_TRY(tdse::lz_launch_next(ctx->prec, sys, N, w, vj + N, j, pb, scal, s));
+                ctx->launches += 1;
+            }
+        }
+        CUDA_TRY(tdse::lz_launch_small(scal, m, dt, s));
+        CUDA_TRY(tdse::lz_launch_combine(sys, N, V, m, scal, (double2 *)c, s));
+        ctx->launches += 2;
+    }
     return TDSE_OK;
 }
 
@@ -548,6 +592,7 @@ static tdse_status propagate_impl(tdse_ctx *ctx, double *c, const double *field,
     tdse_status st = stage_desc(ctx, d, s);
     if (st != TDSE_OK) return st;
     if (nsteps == 0) return TDSE_OK;
+    if (scheme == TDSE_LANCZOS) return propagate_lanczos(ctx, c, sps, dt, nsteps, order, hold, s);
     CUDA_TRY(tdse::launch_prep(ctx->prec, ctx->plan.nblk, ctx->plan.blk.as<int2>(), ctx->sys.as<SysDesc>(), 0, s));
     ctx->launches += 1;
     tdse::EpiArgs a{};
@@ -697,6 +742,8 @@ tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, 
     cudaStream_t s = (cudaStream_t)stream;
     const long long N = ctx->N;
     const long S = (long)samples_per_step * nsteps + 1;
+    if (scheme == TDSE_LANCZOS && (ctx->prec == TDSE_BF16X3 || ctx->prec == TDSE_FP32))
+        return fail(TDSE_ENOTSUP, "batched Lanczos runs on FP64 / float-float contexts only");
     if (ctx->prec == TDSE_BF16X3) {
         if (nsteps == 0) return TDSE_OK;
         return propagate_batch_tc(ctx, c, field, B, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold, s);
@@ -775,6 +822,7 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
     tdse_status st = check_prop_args(ctx, c0, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold);
     if (st != TDSE_OK) return st;
     if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
+    if (scheme == TDSE_LANCZOS) return fail(TDSE_ENOTSUP, "the adjoint covers the RK4 and Taylor schemes");
     if (!weights || !grad_field) return fail(TDSE_EINVAL, "weights and grad_field must not be NULL");
     if (checkpoint_every < 1) return fail(TDSE_EINVAL, "checkpoint_every must be >= 1");
     if (c_final && !aligned16(c_final)) return fail(TDSE_EINVAL, "c_final must be 16-byte aligned");

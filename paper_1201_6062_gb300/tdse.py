@@ -19,11 +19,11 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP = range(6)
-RK4, TAYLOR = 0, 1
+RK4, TAYLOR, LANCZOS = 0, 1, 2
 HOLD_LEFT, HOLD_MID = 0, 1
 FP64, FP32, DF32, BF16X3 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "df32": DF32, "bf16x3": BF16X3}
-SCHEMES = {"rk4": RK4, "taylor": TAYLOR}
+SCHEMES = {"rk4": RK4, "taylor": TAYLOR, "lanczos": LANCZOS}
 
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
