@@ -59,6 +59,8 @@ def _load():
         lib.orc_tridiag_eig.argtypes = [I, _dp, _dp, _dp]
         lib.orc_tridiag_eig.restype = I
         lib.orc_populations.argtypes = [I, I, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.orc_set_gauge.argtypes = [I]
+        lib.orc_vector_potential_sin2.argtypes = [D, D, D, D, D, L, _dp]
         lib.orc_adjoint.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I, I, _dp, _dp, _dp]
         _lib = lib
     return _lib
@@ -168,6 +170,32 @@ def tridiag_eig(d, e):
     if _load().orc_tridiag_eig(m, _p(d), _p(ee), _p(z)) != 0:
         raise RuntimeError("no convergence")
     return d, z
+
+
+def set_gauge(gauge):
+    """'length' (D real symmetric) or 'velocity' (D = i K, K real antisymmetric)."""
+    _load().orc_set_gauge(1 if gauge == "velocity" else 0)
+
+
+class gauge:
+    """Context manager selecting the coupling gauge of every oracle call inside it."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        set_gauge(self.name)
+
+    def __exit__(self, *a):
+        set_gauge("length")
+
+
+def vector_potential_sin2(E0, omega, cycles, t0, h, nsamples):
+    """A(t0 + k h) = -int_0^t E of the sin^2 pulse, 5-point Gauss-Legendre per interval."""
+    out = np.zeros(int(nsamples))
+    _load().orc_vector_potential_sin2(float(E0), float(omega), float(cycles), float(t0), float(h), int(nsamples),
+                                      _p(out))
+    return out
 
 
 def populations(lmax, n, E, c):

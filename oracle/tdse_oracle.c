@@ -41,6 +41,13 @@
 #include <omp.h>
 #endif
 
+/* Coupling gauge (Sec. 5): 0 = length gauge, D real symmetric (upper blocks U_l,
+ * lower blocks U_l^T); 1 = velocity gauge, D = i K with K real antisymmetric
+ * (upper blocks W_l, lower blocks -W_l^T), so that H stays Hermitian. */
+static int g_gauge = 0;
+
+void orc_set_gauge(int g) { g_gauge = g ? 1 : 0; }
+
 int orc_threads(void)
 {
 #ifdef _OPENMP
@@ -62,7 +69,9 @@ void orc_set_threads(int t)
 /*
  * y = D x, the dipole part of the Hamiltonian-vector product (Sec. 4, the
  * block form of H C): block l of the result is
- *     U_l x_{l+1}  (l < lmax)   +   U_{l-1}^T x_{l-1}  (l > 0).
+ *     U_l x_{l+1}  (l < lmax)   +   U_{l-1}^T x_{l-1}  (l > 0)
+ * in the length gauge, and i (U_l x_{l+1} - U_{l-1}^T x_{l-1}) in the velocity
+ * gauge.
  * One sweep over each stored block gives both products: the row dot
  * products feed block l and the row-scaled accumulation feeds block l+1.
  */
@@ -97,7 +106,15 @@ void orc_dmatvec(int lmax, int n, const double *U, const double *x, double *y)
             }
         }
     }
-    for (long a = 0; a < 2 * N; ++a) y[a] = up[a] + dn[a];
+    if (g_gauge == 0) {
+        for (long a = 0; a < 2 * N; ++a) y[a] = up[a] + dn[a];
+    } else {
+        for (long a = 0; a < N; ++a) {          /* i (up - dn) */
+            const double re = up[2 * a] - dn[2 * a], im = up[2 * a + 1] - dn[2 * a + 1];
+            y[2 * a] = -im;
+            y[2 * a + 1] = re;
+        }
+    }
     free(up);
     free(dn);
 }
@@ -518,4 +535,48 @@ long orc_lanczos(int lmax, int n, const double *E, const double *U, double *c, c
     free(V);
     free(w);
     return bad ? -bad : (long)m * nsteps;
+}
+
+/*
+ * Vector potential of the sin^2 pulse of Sec. 5, A(t) = -int_0^t E(t') dt', with
+ * E(t) = E0 sin^2(omega t / (2 ncyc)) sin(omega t) on [0, T], zero after: the
+ * integral over each sample interval [t0 + (k-1) h, t0 + k h] by five-point
+ * Gauss-Legendre quadrature (as Sec. 5 does per time step), accumulated from t = 0.
+ * out[k] = A(t0 + k h), k = 0..nsamples-1 (t0 >= 0; the part [0, t0] is
+ * integrated the same way on a grid of step h).
+ */
+static double sin2_pulse(double t, double E0, double om, double ncyc)
+{
+    const double T = 2.0 * 3.14159265358979323846 * ncyc / om;
+    if (t < 0.0 || t > T) return 0.0;
+    const double s = sin(3.14159265358979323846 * t / T);
+    return E0 * s * s * sin(om * t);
+}
+
+static double gl5(double a, double b, double E0, double om, double ncyc)
+{
+    /* 5-point Gauss-Legendre rule on [-1, 1]: roots of P_5 and their weights in closed form */
+    const double r = 2.0 * sqrt(10.0 / 7.0);
+    const double x1 = sqrt(5.0 - r) / 3.0, x2 = sqrt(5.0 + r) / 3.0;
+    const double w1 = (322.0 + 13.0 * sqrt(70.0)) / 900.0, w2 = (322.0 - 13.0 * sqrt(70.0)) / 900.0;
+    const double x[5] = {0.0, x1, -x1, x2, -x2};
+    const double w[5] = {128.0 / 225.0, w1, w1, w2, w2};
+    const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+    double s = 0.0;
+    for (int q = 0; q < 5; ++q) s += w[q] * sin2_pulse(mid + half * x[q], E0, om, ncyc);
+    return half * s;
+}
+
+void orc_vector_potential_sin2(double E0, double om, double ncyc, double t0, double h, long nsamples, double *out)
+{
+    /* whole intervals [j h, (j+1) h] up to t0, then the remainder, then one
+       interval per sample; endpoints are computed from the index, not summed */
+    double A = 0.0;
+    long j = 0;
+    while ((double)(j + 1) * h <= t0 + 1e-12 * h) { A -= gl5((double)j * h, (double)(j + 1) * h, E0, om, ncyc); ++j; }
+    if ((double)j * h < t0) A -= gl5((double)j * h, t0, E0, om, ncyc);
+    for (long k = 0; k < nsamples; ++k) {
+        if (k > 0) A -= gl5(t0 + (double)(k - 1) * h, t0 + (double)k * h, E0, om, ncyc);
+        out[k] = A;
+    }
 }

@@ -405,3 +405,84 @@ def test_lanczos_mid_hold_is_second_order_in_time():
         errs.append(rel(c, ref))
     r = errs[1] / errs[2]
     assert abs(r / 4.0 - 1) < 0.1, errs
+
+
+# -------------------------------------------------------- velocity gauge --
+
+def dense_K(lmax, n, W):
+    """Dense real antisymmetric coupling: upper blocks W_l, lower blocks -W_l^T."""
+    N = (lmax + 1) * n
+    K = np.zeros((N, N))
+    for l in range(lmax):
+        K[l * n:(l + 1) * n, (l + 1) * n:(l + 2) * n] = W[l]
+        K[(l + 1) * n:(l + 2) * n, l * n:(l + 1) * n] = -W[l].T
+    return K
+
+
+@pytest.mark.parametrize("lmax,n", [(1, 1), (2, 3), (3, 8), (5, 17)])
+def test_velocity_gauge_product_matches_dense_bruteforce(lmax, n):
+    E, W = rand_system(lmax, n, 70 + n)
+    x = inputs.random_state((lmax + 1) * n, 71)
+    D = 1j * dense_K(lmax, n, W)
+    assert np.allclose(D, D.conj().T)                         # Hermitian coupling
+    with oracle.gauge("velocity"):
+        y = oracle.dmatvec(lmax, n, W, x)
+        h = oracle.hmatvec(lmax, n, E, W, 0.3, x)
+    assert rel(y, D @ x) < 1e-14
+    assert rel(h, E * x + 0.3 * (D @ x)) < 1e-14
+
+
+def test_velocity_gauge_propagation_matches_expm_and_keeps_the_norm():
+    lmax, n, g, dt, nsteps = 3, 6, 0.4, 0.05, 40
+    E, W = rand_system(lmax, n, 72)
+    c0 = inputs.random_state((lmax + 1) * n, 73)
+    H = np.diag(E) + g * 1j * dense_K(lmax, n, W)
+    ref = scipy.linalg.expm(-1j * H * dt * nsteps) @ c0
+    with oracle.gauge("velocity"):
+        c, _ = oracle.taylor(lmax, n, E, W, c0, np.full(nsteps + 1, g), dt, nsteps, 20)
+        cl, _ = oracle.lanczos(lmax, n, E, W, c0, np.full(nsteps + 1, g), dt, nsteps, (lmax + 1) * n)
+    assert rel(c, ref) < 1e-12 and rel(cl, ref) < 1e-12
+
+
+def test_velocity_gauge_adjoint_matches_central_differences():
+    lmax, n, dt, nsteps = 2, 4, 0.05, 10
+    E, W = rand_system(lmax, n, 74)
+    c0 = inputs.random_state((lmax + 1) * n, 75)
+    rng = np.random.default_rng(76)
+    F = rng.uniform(-0.8, 0.8, nsteps + 1)
+    w = rng.uniform(0.0, 1.0, (lmax + 1) * n)
+    with oracle.gauge("velocity"):
+        g, _, _ = oracle.adjoint(lmax, n, E, W, c0, F, dt, nsteps, w)
+        h = 1e-6
+        fd = np.zeros_like(F)
+        for m in range(F.size):
+            Fp, Fm = F.copy(), F.copy()
+            Fp[m] += h
+            Fm[m] -= h
+            fd[m] = (_loss(lmax, n, E, W, c0, Fp, dt, nsteps, w, "rk4", 4, 1, 0)
+                     - _loss(lmax, n, E, W, c0, Fm, dt, nsteps, w, "rk4", 4, 1, 0)) / (2 * h)
+    assert rel(g, fd) < 1e-6
+
+
+def _A_closed(t, E0, om, ncyc):
+    """A(t) = -int_0^t E0 sin^2(om t/(2 ncyc)) sin(om t) dt' in closed form (t inside the pulse)."""
+    Om = om / ncyc
+    def prim(s):
+        return 0.5 * E0 * (-np.cos(om * s) / om + np.cos((om + Om) * s) / (2 * (om + Om))
+                           + np.cos((om - Om) * s) / (2 * (om - Om)))
+    return -(prim(t) - prim(0.0))
+
+
+def test_vector_potential_gauss_legendre_matches_the_closed_form():
+    """Sec. 5: A(t) from E(t) by five-point Gauss quadrature per time step."""
+    E0, om, ncyc, h = 0.1, 0.5, 10, 0.01
+    T = 2 * np.pi * ncyc / om
+    t0 = 3.0
+    A = oracle.vector_potential_sin2(E0, om, ncyc, t0, h, 2000)
+    t = t0 + h * np.arange(2000)
+    # the rule is exact to ~h^10 per interval; what remains is the rounding of
+    # ~2300 running additions of |A| <= E0/om: 2300 * 2^-53 * 0.2 ~ 5e-14
+    assert np.max(np.abs(A - _A_closed(t, E0, om, ncyc))) < 1e-13
+    # after the pulse A stays at A(T), which vanishes for a whole number of cycles
+    Aend = oracle.vector_potential_sin2(E0, om, ncyc, T, 0.5, 3)
+    assert np.max(np.abs(Aend)) < 1e-13
