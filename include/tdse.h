@@ -227,6 +227,46 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field,
                          double *loss, void *stream);
 
 /*
+ * Gauge of the coupling (paper Sec. 5).  In the length gauge (the default)
+ * the field factor f(t) is the electric field E(t) and D is real symmetric:
+ * upper blocks U_l, lower blocks U_l^T.  In the velocity gauge f(t) is the
+ * vector potential A(t) and D = i K is Hermitian with K real antisymmetric:
+ * upper blocks i U_l, lower blocks -i U_l^T (the same stored U_l; the
+ * momentum matrix elements and the 1/c factor are folded into them).
+ */
+typedef enum {
+    TDSE_LENGTH = 0,
+    TDSE_VELOCITY = 1
+} tdse_gauge;
+
+/*
+ * tdse_set_gauge — select the gauge of every later call on ctx (products,
+ * propagation, Lanczos, the adjoint and batches).  Groups take the gauge
+ * each member had when tdse_group_create was called.  Synchronises the
+ * device; must not be called while work of ctx is in flight.  For a BF16X3
+ * context the stored transposed dipole planes change sign (exact).
+ * Errors: EINVAL (NULL ctx, unknown gauge), ECUDA.
+ */
+tdse_status tdse_set_gauge(tdse_ctx *ctx, tdse_gauge gauge);
+
+/*
+ * tdse_vector_potential_sin2 — velocity-gauge field samples for the sin^2
+ * pulse E(t) = E0 sin^2(pi t / T) sin(omega t) on [0, T], T = 2 pi cycles /
+ * omega, zero elsewhere (paper Sec. 5): A[k] = -int_0^{t0 + k h} E(t') dt'
+ * for k < nsamples, each interval of length h integrated by the five-point
+ * Gauss-Legendre rule (the integral up to t0 over the intervals [j h,
+ * (j+1) h] below t0 and the remainder), summed in a fixed order.  For
+ * tdse_propagate on the grid t0 + j dt/samples_per_step pass h =
+ * dt/samples_per_step and nsamples = samples_per_step*nsteps + 1.
+ *   A   device, FP64 [nsamples], 8-byte aligned.
+ * Requires omega > 0, cycles > 0, h > 0, t0 >= 0 (all finite),
+ * 1 <= nsamples < 2^31 and t0/h < 2^24.  Asynchronous on `stream`.
+ * Errors: EINVAL, ECUDA.
+ */
+tdse_status tdse_vector_potential_sin2(double E0, double omega, double cycles, double t0, double h,
+                                       long nsamples, double *A, void *stream);
+
+/*
  * Kernel tracing.  While enabled, every block-product launch of the context
  * is bracketed by a pair of CUDA events on its stream, and every kernel the
  * context launches is counted.  tdse_profile_read waits for the recorded

@@ -2,8 +2,9 @@
 // differentiate; the paper has no adjoint).
 //
 // For a step c' = Phi(c; f) built from products k = M(f) x with
-// M(f) = -i (diag(E) + f D) and D real symmetric, the cotangents run
-// backwards through the same products with M^dagger = +i H:
+// M(f) = -i (diag(E) + f D) and D Hermitian (real symmetric in the length
+// gauge, i times a real antisymmetric matrix in the velocity gauge), the
+// cotangents run backwards through the same products with M^dagger = +i H:
 //   g_x = i (E g_k + f D g_k),   dL/df += Re<g_k, -i D x> = Im<D g_k, x>.
 // D g_k comes from the same block mat-vec kernels as the forward pass (its
 // input is the cotangent g_k); this file holds the per-amplitude epilogue of
@@ -47,15 +48,9 @@ adj_epi_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, Ad
     const long long a = (long long)bm.y + threadIdx.x;
     double dot = 0.0;
     if (a < S.N) {
-        const int n = S.n;
-        const int m = (int)(a / n), i = (int)(a - (long long)m * n);
-        // u = D g
-        double ur = 0.0, ui = 0.0;
-        if (m < S.lmax) { const double2 r = S.R[a]; ur = r.x; ui = r.y; }
-        if (m >= 1) {
-            const int b0 = S.sb[m - 1], b1 = S.sb[m];
-            for (int s = b0; s < b1; ++s) { const double2 p = S.P[(long long)s * n + i]; ur += p.x; ui += p.y; }
-        }
+        // u = D g (D Hermitian in either gauge, so the same products serve the adjoint)
+        const double2 u = dx_at(S, a);
+        const double ur = u.x, ui = u.y;
         const double2 g = S.x[a];
         const double e = S.E[a];
         double f;

@@ -299,6 +299,7 @@ static tdse_status propagate_batch_tc(tdse_ctx *ctx, double *c, const double *fi
     A.S = (int)((long)sps * nsteps + 1);
     A.sps = sps;
     A.mode = scheme == TDSE_RK4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
+    A.gauge = ctx->desc.gauge;
     A.order = order;
     A.hold = hold;
     A.half_dt = host_df(0.5 * dt);
@@ -658,6 +659,44 @@ tdse_status tdse_propagate_host(tdse_ctx *ctx, double *c_host, const double *fie
     return tdse_sync(ctx, stream);
 }
 
+tdse_status tdse_set_gauge(tdse_ctx *ctx, tdse_gauge gauge)
+{
+    g_err.clear();
+    if (!ctx) return fail(TDSE_EINVAL, "NULL context");
+    if (gauge != TDSE_LENGTH && gauge != TDSE_VELOCITY) return fail(TDSE_EINVAL, "unknown gauge %d", (int)gauge);
+    if (ctx->desc.gauge == (int)gauge) return TDSE_OK;
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (ctx->prec == TDSE_BF16X3 && ctx->lmax > 0) {
+        // planes 2 and 3 hold U^T (hi, lo); the velocity gauge stores -U^T there
+        const long long plane = (long long)ctx->lmax * ctx->n * ctx->ldb;
+        CUDA_TRY(tdse::launch_tc_negate(ctx->tU.as<__nv_bfloat16>() + 2 * plane, 2 * plane, 0));
+        CUDA_TRY(cudaDeviceSynchronize());
+    }
+    ctx->desc.gauge = (int)gauge;
+    return TDSE_OK;
+}
+
+tdse_status tdse_vector_potential_sin2(double E0, double omega, double cycles, double t0, double h, long nsamples,
+                                       double *A, void *stream)
+{
+    g_err.clear();
+    if (!A) return fail(TDSE_EINVAL, "A is NULL");
+    if (((uintptr_t)A & 7) != 0) return fail(TDSE_EINVAL, "A must be 8-byte aligned");
+    if (!std::isfinite(E0) || !std::isfinite(omega) || !std::isfinite(cycles) || !std::isfinite(t0) ||
+        !std::isfinite(h))
+        return fail(TDSE_EINVAL, "non-finite argument");
+    if (!(omega > 0.0) || !(cycles > 0.0) || !(h > 0.0) || !(t0 >= 0.0))
+        return fail(TDSE_EINVAL, "need omega > 0, cycles > 0, h > 0, t0 >= 0");
+    if (nsamples < 1 || nsamples >= (1L << 31)) return fail(TDSE_EINVAL, "need 1 <= nsamples < 2^31");
+    if (t0 / h >= 16777216.0) return fail(TDSE_EINVAL, "t0/h must be below 2^24");
+    // whole intervals [j h, (j+1) h] below t0: the largest J with J h <= t0 + 1e-12 h
+    long long J = (long long)std::floor(t0 / h);
+    while ((double)(J + 1) * h <= t0 + 1e-12 * h) ++J;
+    while (J > 0 && (double)J * h > t0 + 1e-12 * h) --J;
+    CUDA_TRY(tdse::launch_vector_potential_sin2(E0, omega, cycles, t0, h, nsamples, J, A, (cudaStream_t)stream));
+    return TDSE_OK;
+}
+
 tdse_status tdse_sync(tdse_ctx *ctx, void *stream)
 {
     if (!ctx) return fail(TDSE_EINVAL, "NULL context");
@@ -782,6 +821,7 @@ tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, 
     A.x = ctx->bx.as<double2>();
     A.acc = ctx->bacc.as<double2>();
     A.mode = scheme == TDSE_RK4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
+    A.gauge = ctx->desc.gauge;
     A.order = taylor_order;
     A.hold = taylor_hold;
     A.dt = dt;

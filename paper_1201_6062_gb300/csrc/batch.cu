@@ -59,7 +59,8 @@ bgemm_f32_kernel(BatchArgs A)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int i = i0 + mb + q;
-                    As[kq][mb + q] = (i < n && kk < n) ? Ub[(long long)kk * A.ld + i] : 0.f;
+                    const float u = (i < n && kk < n) ? Ub[(long long)kk * A.ld + i] : 0.f;
+                    As[kq][mb + q] = A.gauge ? -u : u;
                 }
             }
             {

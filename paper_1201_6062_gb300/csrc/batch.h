@@ -21,6 +21,7 @@ struct BatchArgs {
     const __nv_bfloat16 *xin_h, *xin_l;   // bf16 split input planes (tensor path)
     __nv_bfloat16 *xout_h, *xout_l;
     int mode;               // EPI_RK4 (2) or EPI_TAYLOR (3)
+    int gauge;              // 0 length, 1 velocity: the GEMM then sums U X_{l+1} - U^T X_{l-1} and D x = i * that
     int stage, order, hold;
     long long k;
     double dt;
@@ -30,6 +31,7 @@ struct BatchArgs {
 // RK4 stage / Taylor term update in FP64; next product input to xout.
 __device__ __forceinline__ void batch_update(const BatchArgs &A, int b, long long a, double e, double dr, double di)
 {
+    if (A.gauge) { const double t = dr; dr = -di; di = t; }
     const long long q = (long long)b * A.N + a;
     const double *F = A.field + (long long)b * A.S;
     double f;

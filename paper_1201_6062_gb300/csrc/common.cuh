@@ -33,6 +33,8 @@ struct SysDesc {
     double2 *c, *x, *acc;
     void *xq;
     const double *field;
+    int gauge;              // 0: length gauge, D = U-blocks (real symmetric);
+                            // 1: velocity gauge, D = i K with K antisymmetric (Sec. 5)
 };
 
 // A contiguous row range [i0, i1) of block l of system sys; its column
@@ -320,6 +322,32 @@ __device__ __forceinline__ double field_at(const double *F, int sps, long long k
     if (h == 0) return F[k];
     if (h == 2) return F[k + 1];
     return 0.5 * (F[k] + F[k + 1]);
+}
+
+// D x at amplitude a = (m, i) from the block products: the row sum R[a]
+// (U_m x_{m+1}, rows of block m < lmax) and the column partials of block m-1
+// (U_{m-1}^T x_{m-1}, slots sb[m-1] .. sb[m]-1).  Length gauge: D x = R + sum P.
+// Velocity gauge (upper blocks i U_l, lower blocks -i U_l^T, Hermitian):
+// D x = i (R - sum P).  kCG reads R and P around L1.
+template <bool kCG = false>
+__device__ __forceinline__ double2 dx_at(const SysDesc &S, long long a)
+{
+    const int n = S.n;
+    const int m = (int)(a / n), i = (int)(a - (long long)m * n);
+    double rr = 0.0, ri = 0.0, pr = 0.0, pi = 0.0;
+    if (m < S.lmax) {
+        const double2 r = kCG ? __ldcg(S.R + a) : S.R[a];
+        rr = r.x; ri = r.y;
+    }
+    if (m >= 1) {
+        const int b0 = S.sb[m - 1], b1 = S.sb[m];
+        for (int s = b0; s < b1; ++s) {
+            const double2 p = kCG ? __ldcg(S.P + (long long)s * n + i) : S.P[(long long)s * n + i];
+            pr += p.x; pi += p.y;
+        }
+    }
+    if (S.gauge == 0) return make_double2(rr + pr, ri + pi);
+    return make_double2(-(ri - pi), rr - pr);
 }
 
 }  // namespace tdse

@@ -1,5 +1,6 @@
 // Per-amplitude epilogue of one stage (paper Sec. 4: H x = E x + f D x with
-// D x assembled from the row sums R and the column-partial slots P; App. B:
+// D x assembled from the row sums R and the column-partial slots P by dx_at;
+// App. B:
 // the RK4 stage and Taylor term combinations), all in FP64.  Used by the
 // separate epilogue kernel and, fused, by the ring mat-vec kernel.
 #pragma once
@@ -12,20 +13,8 @@ namespace tdse {
 template <class P, bool kCG>
 __device__ __forceinline__ void epi_amp(const SysDesc &S, long long a, const EpiArgs &A)
 {
-    const int n = S.n;
-    const int m = (int)(a / n), i = (int)(a - (long long)m * n);
-    double dr = 0.0, di = 0.0;
-    if (m < S.lmax) {
-        const double2 r = kCG ? __ldcg(S.R + a) : S.R[a];
-        dr = r.x; di = r.y;
-    }
-    if (m >= 1) {
-        const int b0 = S.sb[m - 1], b1 = S.sb[m];
-        for (int s = b0; s < b1; ++s) {
-            const double2 p = kCG ? __ldcg(S.P + (long long)s * n + i) : S.P[(long long)s * n + i];
-            dr += p.x; di += p.y;
-        }
-    }
+    const double2 dx = dx_at<kCG>(S, a);
+    const double dr = dx.x, di = dx.y;
     const double e = S.E[a];
     double f;
     double2 xin;

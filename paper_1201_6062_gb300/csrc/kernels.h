@@ -110,4 +110,8 @@ cudaError_t launch_pop_blocks(const double2 *c, const double *E, int lmax, int n
 cudaError_t launch_pop_totals(const double *part, int L, int B, double *norm,
                               double *bound, double *ionised, cudaStream_t stream);
 
+// A(t0 + k h), k < ns, of the sin^2 pulse (gauge.cu); J = whole intervals below t0.
+cudaError_t launch_vector_potential_sin2(double E0, double omega, double cycles, double t0, double h, long long ns,
+                                         long long J, double *A, cudaStream_t stream);
+
 }  // namespace tdse

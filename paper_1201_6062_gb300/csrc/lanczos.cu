@@ -43,19 +43,6 @@ __device__ __forceinline__ double lz_sum_parts(const double *parts, int n, doubl
     return sh[8];
 }
 
-// D x at amplitude a from the block products (row sums R and column slots P).
-__device__ __forceinline__ double2 lz_dx(const SysDesc &S, long long a)
-{
-    const int n = S.n;
-    const int m = (int)(a / n), i = (int)(a - (long long)m * n);
-    double dr = 0.0, di = 0.0;
-    if (m < S.lmax) { const double2 r = S.R[a]; dr = r.x; di = r.y; }
-    if (m >= 1) {
-        for (int s = S.sb[m - 1]; s < S.sb[m]; ++s) { const double2 p = S.P[(long long)s * n + i]; dr += p.x; di += p.y; }
-    }
-    return make_double2(dr, di);
-}
-
 // parts[b] = sum over the block of |c|^2
 __global__ void __launch_bounds__(256) lz_norm_parts(const SysDesc *__restrict__ sys, const double2 *__restrict__ c,
                                                      double *__restrict__ parts)
@@ -104,7 +91,7 @@ __global__ void __launch_bounds__(256) lz_apply(const SysDesc *__restrict__ sys,
     double v = 0.0;
     if (a < S.N) {
         const double f = field_at(S.field, A.sps, A.k, A.hold ? 1 : 0);
-        const double2 d = lz_dx(S, a);
+        const double2 d = dx_at(S, a);
         const double2 x = vj[a];
         const double e = S.E[a];
         const double2 hw = make_double2(e * x.x + f * d.x, e * x.y + f * d.y);

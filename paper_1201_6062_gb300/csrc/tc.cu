@@ -149,6 +149,7 @@ __device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, d
     const bool rk4 = A.mode == 2;
     const bool from_c = rk4 ? (A.stage == 0) : (A.stage == 1);
     const dfc xin = ld_dfc(from_c ? A.c + q : A.x + q);
+    if (A.gauge) { const float t = dr; dr = -di; di = t; }
     // H x = E x + f D x ;  k = -i H x = (Im, -Re)
     const df hr = df_add(df_mul(e, xin.re), df_mulf(f, dr));
     const df hi = df_add(df_mul(e, xin.im), df_mulf(f, di));
@@ -443,6 +444,20 @@ cudaError_t launch_tc_in(const double2 *c, float4 *cdf, __nv_bfloat16 *xh, __nv_
 {
     const long long tot = N * B;
     tc_in_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(c, cdf, xh, xl, N, n, nb, plane, B);
+    return cudaGetLastError();
+}
+
+// Flip the sign of count bf16 values (exact: the sign bit only).
+__global__ void tc_negate_kernel(__nv_bfloat16 *p, long long count)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < count) p[q] = __hneg(p[q]);
+}
+
+cudaError_t launch_tc_negate(__nv_bfloat16 *p, long long count, cudaStream_t stream)
+{
+    if (count <= 0) return cudaSuccess;
+    tc_negate_kernel<<<(unsigned)((count + 255) / 256), 256, 0, stream>>>(p, count);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ struct TcArgs {
     long long plane;        // elements per state plane: (lmax+1)*nb
     int S, sps;             // field samples per pulse, samples per step
     int mode, stage, order, hold;
+    int gauge;              // 1: velocity gauge (the U^T planes hold -U^T; D x = i * accumulator)
     long long k;
     df half_dt, full_dt, sixth_dt, term_dt;   // dt/2, dt, dt/6 and (Taylor) dt/m as float-float
     const float2 *Edf;      // energies as float-float [N]
@@ -34,6 +35,7 @@ cudaError_t launch_tc_in(const double2 *c, float4 *cdf, __nv_bfloat16 *xh, __nv_
                          int nb, long long plane, int B, cudaStream_t stream);
 cudaError_t launch_tc_field(const double *field, int S, int sps, long long nsteps, int B, float2 *fdf,
                             cudaStream_t stream);
+cudaError_t launch_tc_negate(__nv_bfloat16 *p, long long count, cudaStream_t stream);
 cudaError_t launch_tc_out(const float4 *cdf, double2 *c, long long tot, cudaStream_t stream);
 
 }  // namespace tdse

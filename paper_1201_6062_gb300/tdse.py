@@ -24,6 +24,8 @@ HOLD_LEFT, HOLD_MID = 0, 1
 FP64, FP32, DF32, BF16X3 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "df32": DF32, "bf16x3": BF16X3}
 SCHEMES = {"rk4": RK4, "taylor": TAYLOR, "lanczos": LANCZOS}
+LENGTH, VELOCITY = 0, 1
+GAUGES = {"length": LENGTH, "velocity": VELOCITY}
 
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -46,6 +48,8 @@ _SIGS = {
     "tdse_adjoint": ([_vp, _vp, _vp, _i, _d, _l, _i, _i, _i, _vp, _i, _vp, _vp, _vp, _vp], _i),
     "tdse_profile_enable": ([_vp, _i], _i),
     "tdse_profile_read": ([_vp, ctypes.POINTER(_d), ctypes.POINTER(_l), ctypes.POINTER(_l)], _i),
+    "tdse_set_gauge": ([_vp, _i], _i),
+    "tdse_vector_potential_sin2": ([_d, _d, _d, _d, _d, _l, _vp, _vp], _i),
     "tdse_group_create": ([_vp, _i, ctypes.POINTER(_vp)], _i),
     "tdse_group_destroy": ([_vp], None),
     "tdse_group_propagate": ([_vp, _vp, _vp, _i, _d, _l, _vp], _i),
@@ -102,6 +106,17 @@ def _dev_f64(t, n, name):
     return t
 
 
+def vector_potential_sin2(E0, omega, cycles, t0, h, nsamples, out=None, stream=None):
+    """A(t0 + k h) = -int_0^t E for the sin^2 pulse, k < nsamples (Sec. 5,
+    five-point Gauss-Legendre per interval); a CUDA float64 tensor."""
+    if out is None:
+        out = torch.empty(int(nsamples), dtype=torch.float64, device="cuda")
+    _dev_f64(out, int(nsamples), "out")
+    _check(_lib.tdse_vector_potential_sin2(float(E0), float(omega), float(cycles), float(t0), float(h),
+                                           int(nsamples), _ptr(out), _stream(stream)))
+    return out
+
+
 class Hamiltonian:
     """One field-free Hamiltonian (energies E, upper dipole blocks U_l)
     resident on the GPU in the storage format of `precision`."""
@@ -121,6 +136,7 @@ class Hamiltonian:
         _check(_lib.tdse_create(E.ctypes.data_as(_vp), up, int(lmax), int(n), PRECISIONS[precision], ctypes.byref(h)))
         self._h = h
         self.energies = E
+        self.gauge = "length"
 
     def close(self):
         if getattr(self, "_h", None):
@@ -136,6 +152,11 @@ class Hamiltonian:
     @property
     def handle(self):
         return self._h
+
+    def set_gauge(self, gauge):
+        """"length" (f = E(t), D real symmetric) or "velocity" (f = A(t), D = i K)."""
+        _check(_lib.tdse_set_gauge(self._h, GAUGES[gauge]))
+        self.gauge = gauge
 
     def nfield(self, nsteps, samples_per_step=1):
         return samples_per_step * nsteps + 1

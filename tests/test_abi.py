@@ -59,3 +59,20 @@ def test_host_side_argument_checks(lib):
         [ctypes.c_int] * 3 + [ctypes.c_void_p]
     assert lib.tdse_propagate(None, None, None, 1, 0.01, 1, 0, 4, 0, None) == 1
     assert lib.tdse_version() >= 10000
+
+
+def test_gauge_argument_checks(lib):
+    lib.tdse_set_gauge.restype = ctypes.c_int
+    lib.tdse_set_gauge.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.tdse_set_gauge(None, 1) == 1
+    f = lib.tdse_vector_potential_sin2
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_double] * 5 + [ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p]
+    buf = (ctypes.c_double * 8)()
+    assert f(0.1, 0.5, 10, 0.0, 0.01, 8, None, None) == 1                  # NULL output
+    assert f(0.1, 0.0, 10, 0.0, 0.01, 8, buf, None) == 1                   # omega = 0
+    assert f(0.1, 0.5, 10, 0.0, -0.01, 8, buf, None) == 1                  # h < 0
+    assert f(0.1, 0.5, 10, -1.0, 0.01, 8, buf, None) == 1                  # t0 < 0
+    assert f(0.1, 0.5, 10, 0.0, 0.01, 0, buf, None) == 1                   # no samples
+    assert f(0.1, 0.5, 10, 1e9, 1e-3, 8, buf, None) == 1                   # t0/h too large
+    assert f(float("nan"), 0.5, 10, 0.0, 0.01, 8, buf, None) == 1
