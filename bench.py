@@ -220,8 +220,9 @@ def config_dict(cfg, variant):
 def pulse_sweep_section(args):
     """Many pulses sharing one Hamiltonian (lmax=15, n=1000; E0 log-spaced
     0.01..0.1, omega uniform 0.3..0.9): amplitude-updates/s of the batched
-    bf16x3 tensor-core and FP32 paths next to the single-system FP64 and FP32
-    paths on the same Hamiltonian, and the batched paths' error against the
+    bf16x3 tensor-core, float-float and FP32 paths next to the single-system
+    FP64, float-float and FP32 paths on the same Hamiltonian, and the batched
+    paths' error against the
     CPU oracle on sampled pulses over the timed window."""
     import torch
     import oracle
@@ -242,7 +243,7 @@ def pulse_sweep_section(args):
     refs = {}
     for b in sampled:
         refs[b], _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, W + K)
-    for prec in ("bf16x3", "fp32"):
+    for prec in ("bf16x3", "df32", "fp32"):
         H = tdse.Hamiltonian(E, U, lmax, n, prec)
         c = torch.from_numpy(C0.reshape(-1).copy()).to(dev)
         fw = torch.from_numpy(np.ascontiguousarray(F[:, :W + 1]).reshape(-1)).to(dev)
@@ -264,7 +265,7 @@ def pulse_sweep_section(args):
                      "tensor_or_fma_tflops": flop / (ms / 1e3) / 1e12}
         H.close()
         del c
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "df32", "fp32"):
         H = tdse.Hamiltonian(E, U, lmax, n, prec)
         c = torch.from_numpy(C0[0].copy()).to(dev)
         f = torch.from_numpy(F[0]).to(dev)
@@ -281,6 +282,8 @@ def pulse_sweep_section(args):
         H.close()
     out["speedup_bf16x3_vs_single_fp64"] = out["bf16x3"]["value"] / out["single_fp64"]["value"]
     out["speedup_bf16x3_vs_single_fp32"] = out["bf16x3"]["value"] / out["single_fp32"]["value"]
+    out["speedup_df32_batched_vs_single_df32"] = out["df32"]["value"] / out["single_df32"]["value"]
+    out["speedup_df32_batched_vs_single_fp64"] = out["df32"]["value"] / out["single_fp64"]["value"]
     return out
 
 

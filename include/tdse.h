@@ -194,10 +194,18 @@ tdse_status tdse_populations(tdse_ctx *ctx, const double *c, int B, double *per_
  * Hamiltonian (a pulse sweep).  The B states are advanced together so that
  * each dipole block is read once per stage for all of them (block GEMMs
  * U_l [X_{l+1}] and U_l^T [X_l] with X the n x 2B real matrix of the states'
- * real and imaginary parts).
+ * real and imaginary parts).  By precision of the context:
+ *   FP32    FP32 block GEMM on the FMA pipe.
+ *   DF32    float-float block GEMM (every operand an FP32 hi/lo pair,
+ *           chunked offset accumulators folded into float-float sums): FP64-
+ *           class products for all pulses from FP32 instructions.
+ *   BF16X3  tcgen05 tensor-core GEMM of bf16 hi/lo splits (3 products).
+ *   FP64    the pulses run one after the other on the single-system path
+ *           (as does TDSE_LANCZOS on FP64 and DF32 contexts; FP32 and
+ *           BF16X3 contexts return ENOTSUP for it).
  *   c      device, complex [B][N], in/out.
  *   field  device, FP64 [B][samples_per_step*nsteps + 1].
- * Other arguments as tdse_propagate.  Errors: EINVAL, ENOMEM, ECUDA.
+ * Other arguments as tdse_propagate.  Errors: EINVAL, ENOMEM, ENOTSUP, ECUDA.
  */
 tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, int B,
                                  int samples_per_step, double dt, long nsteps,

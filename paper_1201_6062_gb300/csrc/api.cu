@@ -85,7 +85,8 @@ struct tdse_ctx {
     // adjoint: working state, checkpoints, stage store, cotangents, partial sums
     DevBuf ac, ckpt, store, aG, ag, agc, axq, dots, lparts;
     // batched pulses: FP64 stage inputs / accumulators and the double-buffered product inputs
-    DevBuf bx, bacc, bq;
+    DevBuf bx, bacc, bq, bxmax;
+    float umax_all = 0.f;              // max |U| over all blocks (float-float batched GEMM)
     // Lanczos: Krylov vectors, work vector, partial sums, scalars
     DevBuf lzV, lzw, lzparts, lzscal;
     // bf16x3 tensor-core path: dipole planes, energies as float-float, float-float
@@ -412,6 +413,7 @@ tdse_status tdse_create(const double *energies, const double *dipole_blocks, int
             const double *src = dipole_blocks + (size_t)l * n * n;
             for (size_t q = 0; q < (size_t)n * n; ++q) m = std::fabs(src[q]) > m ? std::fabs(src[q]) : m;
             um[(size_t)l] = std::nextafter((float)m, INFINITY);
+            c->umax_all = um[(size_t)l] > c->umax_all ? um[(size_t)l] : c->umax_all;
         }
         CTRY(c->umax.ensure(sizeof(float) * um.size()));
         CTRY(cudaMemcpy(c->umax.p, um.data(), sizeof(float) * um.size(), cudaMemcpyHostToDevice));
@@ -770,6 +772,63 @@ tdse_status tdse_profile_read(tdse_ctx *ctx, double *mv_ms, long *mv_launches, l
     return TDSE_OK;
 }
 
+// Batch of B pulses with float-float products (batched GEMM, FP64 states).
+static tdse_status propagate_batch_df(tdse_ctx *ctx, double *c, const double *field, int B, int sps, double dt,
+                                      long nsteps, tdse_scheme scheme, int order, int hold, cudaStream_t s)
+{
+    const long long N = ctx->N;
+    const long S = (long)sps * nsteps + 1;
+    CUDA_TRY(ctx->bx.ensure(sizeof(double2) * (size_t)B * N));
+    CUDA_TRY(ctx->bacc.ensure(sizeof(double2) * (size_t)B * N));
+    CUDA_TRY(ctx->bq.ensure(sizeof(float2) * 2 * 2 * (size_t)B * N));
+    CUDA_TRY(ctx->bxmax.ensure(sizeof(int) * 3 * 2 * (size_t)B));
+    CUDA_TRY(cudaMemsetAsync(ctx->bxmax.p, 0, sizeof(int) * 3 * 2 * (size_t)B, s));
+    float2 *q0 = ctx->bq.as<float2>();
+    float2 *q1 = q0 + 2 * (size_t)B * N;
+    int *xm = ctx->bxmax.as<int>();
+    CUDA_TRY(tdse::launch_bprep_df((const double2 *)c, q0, N, B, xm, s));
+    ctx->launches += 1;
+    tdse::BatchArgs A{};
+    A.U = ctx->U.p;
+    A.bstride = ctx->bstride;
+    A.ld = ctx->ld;
+    A.n = ctx->n;
+    A.lmax = ctx->lmax;
+    A.B = B;
+    A.N = N;
+    A.E = ctx->E.as<double>();
+    A.field = field;
+    A.S = (int)S;
+    A.sps = sps;
+    A.c = (double2 *)c;
+    A.x = ctx->bx.as<double2>();
+    A.acc = ctx->bacc.as<double2>();
+    A.mode = scheme == TDSE_RK4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
+    A.gauge = ctx->desc.gauge;
+    A.order = order;
+    A.hold = hold;
+    A.dt = dt;
+    A.xmax = xm;
+    A.umax = ctx->umax_all;
+    long t = 0;
+    for (long k = 0; k < nsteps; ++k) {
+        A.k = k;
+        const int q0s = scheme == TDSE_RK4 ? 0 : 1, q1s = scheme == TDSE_RK4 ? 3 : order;
+        for (int q = q0s; q <= q1s; ++q) {
+            A.stage = q;
+            A.xin2 = (t & 1) ? q1 : q0;
+            A.xout2 = (t & 1) ? q0 : q1;
+            A.xrd = (int)(t % 3);
+            A.xwr = (int)((t + 1) % 3);
+            A.xrs = (int)((t + 2) % 3);
+            CUDA_TRY(tdse::launch_bgemm_df(A, s));
+            ctx->launches += 1;
+            ++t;
+        }
+    }
+    return TDSE_OK;
+}
+
 tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, int B, int samples_per_step,
                                  double dt, long nsteps, tdse_scheme scheme, int taylor_order, int taylor_hold,
                                  void *stream)
@@ -787,9 +846,13 @@ tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, 
         if (nsteps == 0) return TDSE_OK;
         return propagate_batch_tc(ctx, c, field, B, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold, s);
     }
+    if (ctx->prec == TDSE_DF32 && scheme != TDSE_LANCZOS) {
+        if (nsteps == 0) return TDSE_OK;
+        return propagate_batch_df(ctx, c, field, B, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold, s);
+    }
     if (ctx->prec != TDSE_FP32) {
-        // FP64 / float-float products: the pulses run one after the other on
-        // the single-system path.
+        // FP64 products (and batched Lanczos): the pulses run one after the
+        // other on the single-system path.
         for (int b = 0; b < B; ++b) {
             st = propagate_impl(ctx, c + 2 * (size_t)b * N, field + (size_t)b * S, samples_per_step, dt, nsteps,
                                 scheme, taylor_order, taylor_hold, s);

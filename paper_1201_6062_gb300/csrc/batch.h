@@ -20,6 +20,11 @@ struct BatchArgs {
     float *xout;            // FP32 output planes for the next stage
     const __nv_bfloat16 *xin_h, *xin_l;   // bf16 split input planes (tensor path)
     __nv_bfloat16 *xout_h, *xout_l;
+    const float2 *xin2;     // float-float input planes [2B][N] (h, l) (float-float path)
+    float2 *xout2;
+    int *xmax;              // 3 rotating slot vectors [3][2B]: max |x| per plane (float bits, >= 0)
+    int xrd, xwr, xrs;      // slot vector read by this launch, written by its epilogue, cleared by it
+    float umax;             // max |U| over all blocks
     int mode;               // EPI_RK4 (2) or EPI_TAYLOR (3)
     int gauge;              // 0 length, 1 velocity: the GEMM then sums U X_{l+1} - U^T X_{l-1} and D x = i * that
     int stage, order, hold;
@@ -29,7 +34,7 @@ struct BatchArgs {
 
 // One pulse b, amplitude a: Dx = (dr, di) from the GEMM; k = -i (E x + f Dx);
 // RK4 stage / Taylor term update in FP64; next product input to xout.
-__device__ __forceinline__ void batch_update(const BatchArgs &A, int b, long long a, double e, double dr, double di)
+__device__ __forceinline__ double2 batch_update(const BatchArgs &A, int b, long long a, double e, double dr, double di)
 {
     if (A.gauge) { const double t = dr; dr = -di; di = t; }
     const long long q = (long long)b * A.N + a;
@@ -93,9 +98,17 @@ __device__ __forceinline__ void batch_update(const BatchArgs &A, int b, long lon
         A.xout_l[pr] = __double2bfloat16(out.x - (double)__bfloat162float(hr16));
         A.xout_l[pi] = __double2bfloat16(out.y - (double)__bfloat162float(hi16));
     }
+    if (A.xout2) {
+        const float rh = __double2float_rn(out.x), ih = __double2float_rn(out.y);
+        A.xout2[pr] = make_float2(rh, __double2float_rn(out.x - (double)rh));
+        A.xout2[pi] = make_float2(ih, __double2float_rn(out.y - (double)ih));
+    }
+    return out;
 }
 
 cudaError_t launch_bgemm_f32(const BatchArgs &A, cudaStream_t stream);
+cudaError_t launch_bgemm_df(const BatchArgs &A, cudaStream_t stream);
+cudaError_t launch_bprep_df(const double2 *c, float2 *planes, long long N, int B, int *xmax_slot, cudaStream_t stream);
 cudaError_t launch_bprep_f32(const double2 *c, float *planes, long long N, int B, cudaStream_t stream);
 
 }  // namespace tdse

@@ -31,8 +31,8 @@ def sweep(lmax, n, B, nsteps, sps, dt=0.02, seed=3):
 @pytest.mark.parametrize("prec", ["fp32", "fp64", "df32"])
 @pytest.mark.parametrize("lmax,n,B", [(3, 130, 5), (2, 1000, 64), (0, 40, 3), (4, 257, 1), (1, 17, 70)])
 def test_batched_rk4_matches_oracle_per_pulse(tdse_lib, prec, lmax, n, B):
-    if prec != "fp32" and B > 8:
-        pytest.skip("FP64-class batches run pulse by pulse; covered by the small cases")
+    if prec == "fp64" and B > 8:
+        pytest.skip("FP64 batches run pulse by pulse; covered by the small cases")
     dt, nsteps, sps = 0.02, 40, 1
     E, U, F, C0 = sweep(lmax, n, B, nsteps, sps)
     H = tdse_lib.Hamiltonian(E, U, lmax, n, prec)
@@ -56,6 +56,54 @@ def test_batched_taylor_matches_oracle(tdse_lib, K, hold, sps):
     for b in range(B):
         ref, _ = oracle.taylor(lmax, n, E, U, C0[b], F[b], dt, nsteps, K, samples_per_step=sps, hold=hold)
         assert rel(got[b], ref) < 1e-5, b
+
+
+@pytest.mark.parametrize("K,hold,sps", [(6, 0, 1), (5, 1, 2)])
+def test_df32_batched_taylor_matches_oracle(tdse_lib, K, hold, sps):
+    lmax, n, B, dt, nsteps = 3, 300, 9, 0.02, 25
+    E, U, F, C0 = sweep(lmax, n, B, nsteps, sps)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "df32")
+    c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(c, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps, "taylor", order=K, hold=hold,
+                      samples_per_step=sps)
+    got = c.cpu().numpy().reshape(B, -1)
+    for b in range(B):
+        ref, _ = oracle.taylor(lmax, n, E, U, C0[b], F[b], dt, nsteps, K, samples_per_step=sps, hold=hold)
+        assert rel(got[b], ref) < 1e-10, b
+
+
+def test_df32_batched_scale_and_zero_states(tdse_lib):
+    """The offset accumulators take their scale from the largest amplitude of
+    the stage input: states scaled by 1e3 or 1e-3, and all-zero pulses
+    (which stay zero), keep the FP64-class tolerance."""
+    lmax, n, B, dt, nsteps = 2, 333, 6, 0.02, 30
+    E, U, F, C0 = sweep(lmax, n, B, nsteps, 1)
+    C0 = C0 * np.array([1e3, 1e-3, 0.0, 1.0, 7.0, 0.0])[:, None]
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "df32")
+    c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(c, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps)
+    got = c.cpu().numpy().reshape(B, -1)
+    for b in range(B):
+        if not np.any(C0[b]):
+            assert not np.any(got[b])
+            continue
+        ref, _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, nsteps)
+        assert rel(got[b], ref) < 1e-10, b
+
+
+def test_df32_batched_long_window_stays_fp64_class(tdse_lib):
+    """600 steps of a pulse sweep on the ground state: the float-float GEMM
+    stays within 1e-10 of the FP64 oracle."""
+    lmax, n, B, dt, nsteps = 3, 500, 4, 0.02, 600
+    E, U, F, _ = sweep(lmax, n, B, nsteps, 2)
+    C0 = np.stack([inputs.ground_state(lmax, n)] * B)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "df32")
+    c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(c, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps, samples_per_step=2)
+    got = c.cpu().numpy().reshape(B, -1)
+    for b in range(B):
+        ref, _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, nsteps, samples_per_step=2)
+        assert rel(got[b], ref) < 1e-10, b
 
 
 def test_batched_equals_single_instance_fp32_per_pulse_within_rounding(tdse_lib):

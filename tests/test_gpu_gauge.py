@@ -98,7 +98,7 @@ def test_velocity_adjoint_matches_oracle(T):
     assert rel(cT.cpu().numpy(), cref) < 1e-11
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 5e-5), ("bf16x3", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("df32", 1e-10), ("fp32", 5e-5), ("bf16x3", 1e-5)])
 def test_velocity_batch_matches_oracle(T, prec, tol):
     lmax, n, dt, nsteps, B = 3, 70, 0.02, 100, 5
     E, U = system(lmax, n, 18)
