@@ -61,6 +61,10 @@ def _load():
         lib.orc_populations.argtypes = [I, I, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         lib.orc_set_gauge.argtypes = [I]
         lib.orc_vector_potential_sin2.argtypes = [D, D, D, D, D, L, _dp]
+        lib.orc_rkf45_tableau.argtypes = [_dp, _dp, _dp, _dp]
+        lib.orc_rkf45.argtypes = [I, I, _dp, _dp, _dp, I, D, D, D, D, D, D, D, D, D, D, L,
+                                  ctypes.POINTER(L), _dp]
+        lib.orc_rkf45.restype = L
         lib.orc_adjoint.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I, I, _dp, _dp, _dp]
         _lib = lib
     return _lib
@@ -158,6 +162,33 @@ def lanczos(lmax, n, E, U, c0, F, dt, nsteps, m, samples_per_step=1, hold=1):
     if r < 0:
         raise RuntimeError("tridiagonal eigensolver did not converge in %d steps" % (-r))
     return c, r
+
+
+def rkf45_tableau():
+    """Fehlberg 4(5) coefficients as the oracle holds them: (c[6], a[6x6], b5[6], b4[6])."""
+    c, a, b5, b4 = np.zeros(6), np.zeros(36), np.zeros(6), np.zeros(6)
+    _load().orc_rkf45_tableau(_p(c), _p(a), _p(b5), _p(b4))
+    return c, a.reshape(6, 6), b5, b4
+
+
+def rkf45(lmax, n, E, U, c0, t0, t1, dt0, tol, field="sin2", E0=0.0, omega=1.0, cycles=10, a0=0.0,
+          dt_min=0.0, dt_max=np.inf, max_attempts=10 ** 7):
+    """Adaptive Runge-Kutta-Fehlberg 4(5) from t0 to t1.
+
+    field: "sin2" (the Sec. 5 pulse: E(t) in the length gauge, A(t) from a0 by
+    Gauss-Legendre in the velocity gauge) or "const" (f = E0).
+    Returns (c, info) with info = dict(accepted, rejected, forced, t, dt, err, A, products)."""
+    E, U = _dims(E, U, lmax, n)
+    c, cv = _cvec(c0)
+    st = (ctypes.c_long * 3)()
+    tout = np.zeros(4)
+    kind = {"sin2": 0, "const": 1}[field]
+    prods = _load().orc_rkf45(lmax, n, _p(E), _p(U), _p(cv), kind, float(E0), float(omega), float(cycles),
+                              float(a0), float(t0), float(t1), float(dt0), float(tol), float(dt_min),
+                              float(min(dt_max, 1e300)), int(max_attempts), st, _p(tout))
+    info = dict(accepted=st[0], rejected=st[1], forced=st[2], t=tout[0], dt=tout[1], err=tout[2], A=tout[3],
+                products=prods)
+    return c, info
 
 
 def tridiag_eig(d, e):

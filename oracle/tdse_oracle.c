@@ -580,3 +580,113 @@ void orc_vector_potential_sin2(double E0, double om, double ncyc, double t0, dou
         out[k] = A;
     }
 }
+
+/*
+ * Runge-Kutta-Fehlberg 4(5) (App. B names the embedded pair; its
+ * coefficients are Fehlberg's, NASA TR R-315, 1969).  Six derivatives per
+ * attempt; the fifth-order combination advances the state (the paper takes
+ * the 5th-order solution) and the difference of the two combinations
+ * estimates the local error.
+ *
+ * Step-size control (the paper fixes no rule; reading stated in the design
+ * notes): the error of an attempt is err = |e|_2 / |c|_2 with
+ * e = h sum (b5_i - b4_i) k_i.  The attempt is accepted when err <= tol or
+ * when h <= dt_min (a forced acceptance).  The next step is
+ * h * min(5, max(0.2, 0.9 (tol/err)^(1/5))) (5 when err = 0), kept inside
+ * [dt_min, dt_max].  An attempt never steps past t1: h = min(dt, t1 - t).
+ *
+ * Field: kind 1 is the constant f = E0.  Kind 0 is the sin^2 pulse of Sec. 5;
+ * in the length gauge f(t) = E(t), in the velocity gauge f(t) = A(t), taken
+ * from A at the last accepted time by the five-point Gauss-Legendre rule
+ * over [t_n, t] (A(t0) = a0 is given).
+ */
+static const double rkf_c[6] = {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0};
+static const double rkf_a[6][5] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0 / 4.0, 0.0, 0.0, 0.0, 0.0},
+    {3.0 / 32.0, 9.0 / 32.0, 0.0, 0.0, 0.0},
+    {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0.0, 0.0},
+    {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0.0},
+    {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+static const double rkf_b5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+static const double rkf_b4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+
+void orc_rkf45_tableau(double *c, double *a, double *b5, double *b4)
+{
+    for (int i = 0; i < 6; ++i) {
+        c[i] = rkf_c[i];
+        b5[i] = rkf_b5[i];
+        b4[i] = rkf_b4[i];
+        for (int j = 0; j < 6; ++j) a[i * 6 + j] = j < 5 ? rkf_a[i][j] : 0.0;
+    }
+}
+
+static double rkf_field(int kind, double E0, double om, double ncyc, double tn, double An, double t)
+{
+    if (kind == 1) return E0;
+    if (g_gauge == 0) return sin2_pulse(t, E0, om, ncyc);
+    return An - gl5(tn, t, E0, om, ncyc);
+}
+
+/* stats: [accepted, rejected, forced]; tout: [t reached, next dt, err of the
+   last attempt, A at the reached time].  Returns the number of products. */
+long orc_rkf45(int lmax, int n, const double *E, const double *U, double *c, int kind, double E0, double om,
+               double ncyc, double a0, double t0, double t1, double dt0, double tol, double dt_min, double dt_max,
+               long max_attempts, long *stats, double *tout)
+{
+    const long N = (long)(lmax + 1) * n;
+    double *k = (double *)malloc(sizeof(double) * 2 * N * 6);
+    double *x = (double *)malloc(sizeof(double) * 2 * N);
+    double t = t0, dt = dt0, A = a0, err = 0.0;
+    long acc = 0, rej = 0, forced = 0, att = 0;
+    while (t < t1 && att < max_attempts) {
+        const double h = dt < t1 - t ? dt : t1 - t;
+        const int last = !(dt < t1 - t);
+        for (int s = 0; s < 6; ++s) {
+            for (long q = 0; q < 2 * N; ++q) {
+                double v = c[q];
+                for (int j = 0; j < s; ++j) v += h * rkf_a[s][j] * k[(long)j * 2 * N + q];
+                x[q] = v;
+            }
+            deriv(lmax, n, E, U, rkf_field(kind, E0, om, ncyc, t, A, t + rkf_c[s] * h), x, k + (long)s * 2 * N);
+        }
+        double ee = 0.0, cc = 0.0;
+        for (long q = 0; q < 2 * N; ++q) {
+            double e = 0.0, y = c[q];
+            for (int s = 0; s < 6; ++s) {
+                e += h * (rkf_b5[s] - rkf_b4[s]) * k[(long)s * 2 * N + q];
+                y += h * rkf_b5[s] * k[(long)s * 2 * N + q];
+            }
+            ee += e * e;
+            cc += c[q] * c[q];
+            x[q] = y;
+        }
+        err = cc > 0.0 ? sqrt(ee / cc) : 0.0;
+        ++att;
+        const int ok = err <= tol;
+        if (ok || h <= dt_min) {
+            if (!ok) ++forced;
+            memcpy(c, x, sizeof(double) * 2 * N);
+            if (kind == 0 && g_gauge == 1) A -= gl5(t, t + h, E0, om, ncyc);
+            t = last ? t1 : t + h;
+            ++acc;
+        } else {
+            ++rej;
+        }
+        double fac = err > 0.0 ? 0.9 * pow(tol / err, 0.2) : 5.0;
+        fac = fac < 0.2 ? 0.2 : (fac > 5.0 ? 5.0 : fac);
+        double nd = h * fac;
+        nd = nd < dt_min ? dt_min : (nd > dt_max ? dt_max : nd);
+        dt = nd;
+    }
+    free(k);
+    free(x);
+    stats[0] = acc;
+    stats[1] = rej;
+    stats[2] = forced;
+    tout[0] = t;
+    tout[1] = dt;
+    tout[2] = err;
+    tout[3] = A;
+    return 6 * att;
+}

@@ -486,3 +486,127 @@ def test_vector_potential_gauss_legendre_matches_the_closed_form():
     # after the pulse A stays at A(T), which vanishes for a whole number of cycles
     Aend = oracle.vector_potential_sin2(E0, om, ncyc, T, 0.5, 3)
     assert np.max(np.abs(Aend)) < 1e-13
+
+
+# ---------------------------------------------------- Runge-Kutta-Fehlberg --
+
+def test_rkf45_tableau_satisfies_the_order_conditions():
+    """Butcher's rooted-tree conditions: the 5th-order weights meet all 17
+    conditions up to order 5, the 4th-order weights the 8 up to order 4 (and
+    miss order 5), and every row of A sums to its node c_i."""
+    c, A, b5, b4 = oracle.rkf45_tableau()
+    assert np.allclose(A.sum(axis=1), c, atol=1e-15)
+    assert np.all(np.triu(A) == 0.0)            # explicit
+    Ac = A @ c
+    conds = [
+        (lambda b: b.sum(), 1.0),
+        (lambda b: b @ c, 1 / 2),
+        (lambda b: b @ c ** 2, 1 / 3), (lambda b: b @ Ac, 1 / 6),
+        (lambda b: b @ c ** 3, 1 / 4), (lambda b: b @ (c * Ac), 1 / 8), (lambda b: b @ (A @ c ** 2), 1 / 12),
+        (lambda b: b @ (A @ Ac), 1 / 24),
+    ]
+    order5 = [
+        (lambda b: b @ c ** 4, 1 / 5), (lambda b: b @ (c ** 2 * Ac), 1 / 10), (lambda b: b @ Ac ** 2, 1 / 20),
+        (lambda b: b @ (c * (A @ c ** 2)), 1 / 15), (lambda b: b @ (c * (A @ Ac)), 1 / 30),
+        (lambda b: b @ (A @ c ** 3), 1 / 20), (lambda b: b @ (A @ (c * Ac)), 1 / 40),
+        (lambda b: b @ (A @ (A @ c ** 2)), 1 / 60), (lambda b: b @ (A @ (A @ Ac)), 1 / 120),
+    ]
+    for f, v in conds + order5:
+        assert abs(f(b5) - v) < 1e-14
+    for f, v in conds:
+        assert abs(f(b4) - v) < 1e-14
+    assert max(abs(f(b4) - v) for f, v in order5) > 1e-4
+
+
+def _rkf_polys(z):
+    """Stability functions of Fehlberg's pair: the 5th-order weights give the
+    exponential series to z^5 plus z^6/2080; the 4th-order weights give it to
+    z^4 plus z^5/104 (both from the product b6 a65 a54 a43 a32 a21 and
+    b5 a54 a43 a32 a21 of the published coefficients)."""
+    base = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    return base + z ** 5 / 120 + z ** 6 / 2080, base + z ** 5 / 104
+
+
+def test_rkf45_single_step_on_the_field_free_system_is_the_stability_polynomial():
+    lmax, n, h = 2, 5, 0.3
+    E, U = rand_system(lmax, n, 80)
+    c0 = inputs.random_state((lmax + 1) * n, 81)
+    c, info = oracle.rkf45(lmax, n, E, U, c0, 0.0, h, h, 1e300, field="const", E0=0.0)
+    R5, R4 = _rkf_polys(-1j * E * h)
+    assert info["accepted"] == 1 and info["rejected"] == 0
+    assert rel(c, R5 * c0) < 1e-14
+    err = np.linalg.norm((R5 - R4) * c0) / np.linalg.norm(c0)
+    # e = h sum (b5 - b4) k cancels terms of size |c|: its rounding is absolute, ~2^-52 |c|
+    assert abs(info["err"] - err) < 1e-14 and err > 1e-7
+
+
+def test_rkf45_controller_matches_an_independent_simulation():
+    """Field-free system: each attempt's error is known in closed form, so
+    the accept/reject sequence and step sizes can be replayed in numpy."""
+    lmax, n = 1, 6
+    E, U = rand_system(lmax, n, 82)
+    c0 = inputs.random_state((lmax + 1) * n, 83)
+    t0, t1, dt0, tol, dtmin, dtmax = 0.0, 7.3, 1.7, 1e-7, 1e-4, 0.9
+    c, info = oracle.rkf45(lmax, n, E, U, c0, t0, t1, dt0, tol, field="const", E0=0.0, dt_min=dtmin, dt_max=dtmax)
+    t, dt, cc, acc, rej = t0, dt0, c0.copy(), 0, 0
+    while t < t1:
+        h = min(dt, t1 - t)
+        R5, R4 = _rkf_polys(-1j * E * h)
+        err = np.linalg.norm((R5 - R4) * cc) / np.linalg.norm(cc)
+        if err <= tol or h <= dtmin:
+            cc = R5 * cc
+            t = t1 if dt >= t1 - t else t + h
+            acc += 1
+        else:
+            rej += 1
+        fac = min(5.0, max(0.2, 0.9 * (tol / err) ** 0.2)) if err > 0 else 5.0
+        dt = min(dtmax, max(dtmin, h * fac))
+    assert (info["accepted"], info["rejected"]) == (acc, rej)
+    assert rej >= 1 and acc > 5                   # the first step is too long and gets rejected
+    assert info["t"] == t1
+    assert rel(c, cc) < 1e-12
+
+
+def test_rkf45_constant_field_matches_expm_and_the_error_follows_tol():
+    lmax, n, g, T = 3, 6, 0.5, 6.0
+    E, U = rand_system(lmax, n, 84)
+    c0 = inputs.random_state((lmax + 1) * n, 85)
+    H = np.diag(E) + g * dense_D(lmax, n, U)
+    ref = scipy.linalg.expm(-1j * H * T) @ c0
+    errs = []
+    for tol in (1e-6, 1e-9, 1e-12):
+        c, info = oracle.rkf45(lmax, n, E, U, c0, 0.0, T, 0.1, tol, field="const", E0=g)
+        errs.append(rel(c, ref))
+        assert info["t"] == T and info["forced"] == 0
+    assert errs[2] < 1e-10
+    assert errs[0] / errs[1] > 30 and errs[1] / errs[2] > 30
+
+
+@pytest.mark.parametrize("gauge", ["length", "velocity"])
+def test_rkf45_sin2_pulse_matches_an_independent_integrator(gauge):
+    """Time-dependent field: DOP853 at tight tolerance on the dense matrix,
+    with E(t) (length) or the closed-form A(t) (velocity gauge)."""
+    lmax, n, E0, om, cyc = 2, 4, 0.6, 1.1, 2
+    E, U = rand_system(lmax, n, 86)
+    c0 = inputs.random_state((lmax + 1) * n, 87)
+    T = 2 * np.pi * cyc / om
+    D = dense_D(lmax, n, U) if gauge == "length" else 1j * dense_K(lmax, n, U)
+
+    def f(t):
+        return float(inputs.pulse(t, E0, om, cycles=cyc)) if gauge == "length" else _A_closed(t, E0, om, cyc)
+
+    def rhs(t, y):
+        cc = y[: y.size // 2] + 1j * y[y.size // 2:]
+        d = -1j * (E * cc + f(t) * (D @ cc))
+        return np.concatenate([d.real, d.imag])
+
+    sol = scipy.integrate.solve_ivp(rhs, (0.0, T), np.concatenate([c0.real, c0.imag]), method="DOP853",
+                                    rtol=1e-13, atol=1e-15)
+    y = sol.y[:, -1]
+    ref = y[: y.size // 2] + 1j * y[y.size // 2:]
+    with oracle.gauge(gauge):
+        c, info = oracle.rkf45(lmax, n, E, U, c0, 0.0, T, 0.05, 1e-11, field="sin2", E0=E0, omega=om, cycles=cyc)
+    assert info["t"] == T
+    assert rel(c, ref) < 1e-9
+    if gauge == "velocity":
+        assert abs(info["A"] - _A_closed(T, E0, om, cyc)) < 1e-13
