@@ -593,7 +593,9 @@ void orc_vector_potential_sin2(double E0, double om, double ncyc, double t0, dou
  * e = h sum (b5_i - b4_i) k_i.  The attempt is accepted when err <= tol or
  * when h <= dt_min (a forced acceptance).  The next step is
  * h * min(5, max(0.2, 0.9 (tol/err)^(1/5))) (5 when err = 0), kept inside
- * [dt_min, dt_max].  An attempt never steps past t1: h = min(dt, t1 - t).
+ * [dt_min, dt_max].  An attempt never steps past t1, and one that would
+ * leave less than 1e-12 of the remaining interval takes all of it (no
+ * round-off-sized final step).
  *
  * Field: kind 1 is the constant f = E0.  Kind 0 is the sin^2 pulse of Sec. 5;
  * in the length gauge f(t) = E(t), in the velocity gauge f(t) = A(t), taken
@@ -640,8 +642,9 @@ long orc_rkf45(int lmax, int n, const double *E, const double *U, double *c, int
     double t = t0, dt = dt0, A = a0, err = 0.0;
     long acc = 0, rej = 0, forced = 0, att = 0;
     while (t < t1 && att < max_attempts) {
-        const double h = dt < t1 - t ? dt : t1 - t;
-        const int last = !(dt < t1 - t);
+        /* the attempt that would leave less than 1e-12 of the interval takes it all */
+        const int last = !(dt < (t1 - t) * (1.0 - 1e-12));
+        const double h = last ? t1 - t : dt;
         for (int s = 0; s < 6; ++s) {
             for (long q = 0; q < 2 * N; ++q) {
                 double v = c[q];

@@ -550,12 +550,13 @@ def test_rkf45_controller_matches_an_independent_simulation():
     c, info = oracle.rkf45(lmax, n, E, U, c0, t0, t1, dt0, tol, field="const", E0=0.0, dt_min=dtmin, dt_max=dtmax)
     t, dt, cc, acc, rej = t0, dt0, c0.copy(), 0, 0
     while t < t1:
-        h = min(dt, t1 - t)
+        last = not dt < (t1 - t) * (1 - 1e-12)
+        h = t1 - t if last else dt
         R5, R4 = _rkf_polys(-1j * E * h)
         err = np.linalg.norm((R5 - R4) * cc) / np.linalg.norm(cc)
         if err <= tol or h <= dtmin:
             cc = R5 * cc
-            t = t1 if dt >= t1 - t else t + h
+            t = t1 if last else t + h
             acc += 1
         else:
             rej += 1
