@@ -275,6 +275,62 @@ tdse_status tdse_vector_potential_sin2(double E0, double omega, double cycles, d
                                        long nsamples, double *A, void *stream);
 
 /*
+ * Field given as a function of time, for propagators that choose their own
+ * stage times (tdse_propagate_rkf45).
+ *   TDSE_FIELD_SIN2   the sin^2 pulse of Sec. 5: E(t) = E0 sin^2(pi t/T)
+ *                     sin(omega t) on [0, T], T = 2 pi cycles/omega, zero
+ *                     elsewhere.  Length gauge: f(t) = E(t).  Velocity gauge:
+ *                     f(t) = A(t), A(t0) = a0 and A advanced over each
+ *                     accepted step (and to each stage time) by the
+ *                     five-point Gauss-Legendre rule.
+ *   TDSE_FIELD_CONST  f(t) = E0 (omega, cycles, a0 unused).
+ */
+typedef enum {
+    TDSE_FIELD_SIN2 = 0,
+    TDSE_FIELD_CONST = 1
+} tdse_field_kind;
+
+typedef struct {
+    int kind;               /* tdse_field_kind */
+    double E0, omega, cycles;
+    double a0;              /* velocity gauge, sin^2: A(t0) */
+} tdse_field_fn;
+
+typedef struct {
+    long accepted, rejected, forced;   /* forced: accepted at h <= dt_min with err > tol */
+    double t;               /* time reached (t1 unless max_attempts ran out) */
+    double dt;              /* step the controller proposes next */
+    double err;             /* error estimate of the last attempt */
+    double a;               /* velocity gauge, sin^2: A(t) */
+} tdse_rkf_stats;
+
+/*
+ * tdse_propagate_rkf45 — adaptive Runge-Kutta-Fehlberg 4(5) from t0 to t1
+ * (App. B names the embedded pair; Fehlberg's 1969 coefficients).  Each
+ * attempt takes six products; the 5th-order combination advances c (as in
+ * the paper) and e = h sum (b5_i - b4_i) k_i estimates the local error.
+ * Controller: err = |e|_2 / |c|_2; accept when err <= tol, or (forced)
+ * when the step is at dt_min;
+ * next step h * clamp(0.9 (tol/err)^(1/5), 0.2, 5) within [dt_min, dt_max];
+ * no attempt passes t1, and one that would leave less than 1e-12 of the
+ * remaining interval takes all of it.  The decisions are taken on the device; the host
+ * reads the controller between chunks of attempts, so the call returns with
+ * the stream synchronised.
+ *   c             device, complex [N], in: c(t0), out: c(t reached).
+ *   field         host, the field function (copied).
+ *   t0 <= t1, dt0 > 0, tol > 0, 0 <= dt_min <= dt_max (dt_max > 0): finite.
+ *   max_attempts  >= 0: bound on accepted plus rejected attempts.
+ *   stats         host or NULL.
+ * Errors: EINVAL (also when the step underflows: tol unattainable with
+ * dt_min = 0; c then holds the last accepted state), ENOTSUP (BF16X3
+ * context), ECUDA, ETIMEOUT.
+ */
+tdse_status tdse_propagate_rkf45(tdse_ctx *ctx, double *c, const tdse_field_fn *field,
+                                 double t0, double t1, double dt0, double tol, double dt_min,
+                                 double dt_max, long max_attempts, tdse_rkf_stats *stats,
+                                 void *stream);
+
+/*
  * Kernel tracing.  While enabled, every block-product launch of the context
  * is bracketed by a pair of CUDA events on its stream, and every kernel the
  * context launches is counted.  tdse_profile_read waits for the recorded

@@ -180,14 +180,14 @@ def rkf45(lmax, n, E, U, c0, t0, t1, dt0, tol, field="sin2", E0=0.0, omega=1.0, 
     Returns (c, info) with info = dict(accepted, rejected, forced, t, dt, err, A, products)."""
     E, U = _dims(E, U, lmax, n)
     c, cv = _cvec(c0)
-    st = (ctypes.c_long * 3)()
+    st = (ctypes.c_long * 4)()
     tout = np.zeros(4)
     kind = {"sin2": 0, "const": 1}[field]
     prods = _load().orc_rkf45(lmax, n, _p(E), _p(U), _p(cv), kind, float(E0), float(omega), float(cycles),
                               float(a0), float(t0), float(t1), float(dt0), float(tol), float(dt_min),
                               float(min(dt_max, 1e300)), int(max_attempts), st, _p(tout))
-    info = dict(accepted=st[0], rejected=st[1], forced=st[2], t=tout[0], dt=tout[1], err=tout[2], A=tout[3],
-                products=prods)
+    info = dict(accepted=st[0], rejected=st[1], forced=st[2], stalled=bool(st[3]), t=tout[0], dt=tout[1],
+                err=tout[2], A=tout[3], products=prods)
     return c, info
 
 

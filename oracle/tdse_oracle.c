@@ -591,7 +591,9 @@ void orc_vector_potential_sin2(double E0, double om, double ncyc, double t0, dou
  * Step-size control (the paper fixes no rule; reading stated in the design
  * notes): the error of an attempt is err = |e|_2 / |c|_2 with
  * e = h sum (b5_i - b4_i) k_i.  The attempt is accepted when err <= tol or
- * when h <= dt_min (a forced acceptance).  The next step is
+ * when the step is at dt_min (h <= dt_min or the proposal dt <= dt_min: a
+ * forced acceptance).  When the next step can no longer move t (tol
+ * unattainable with dt_min = 0) the run stops and reports it.  The next step is
  * h * min(5, max(0.2, 0.9 (tol/err)^(1/5))) (5 when err = 0), kept inside
  * [dt_min, dt_max].  An attempt never steps past t1, and one that would
  * leave less than 1e-12 of the remaining interval takes all of it (no
@@ -630,7 +632,7 @@ static double rkf_field(int kind, double E0, double om, double ncyc, double tn, 
     return An - gl5(tn, t, E0, om, ncyc);
 }
 
-/* stats: [accepted, rejected, forced]; tout: [t reached, next dt, err of the
+/* stats: [accepted, rejected, forced, stalled]; tout: [t reached, next dt, err of the
    last attempt, A at the reached time].  Returns the number of products. */
 long orc_rkf45(int lmax, int n, const double *E, const double *U, double *c, int kind, double E0, double om,
                double ncyc, double a0, double t0, double t1, double dt0, double tol, double dt_min, double dt_max,
@@ -640,7 +642,7 @@ long orc_rkf45(int lmax, int n, const double *E, const double *U, double *c, int
     double *k = (double *)malloc(sizeof(double) * 2 * N * 6);
     double *x = (double *)malloc(sizeof(double) * 2 * N);
     double t = t0, dt = dt0, A = a0, err = 0.0;
-    long acc = 0, rej = 0, forced = 0, att = 0;
+    long acc = 0, rej = 0, forced = 0, att = 0, stalled = 0;
     while (t < t1 && att < max_attempts) {
         /* the attempt that would leave less than 1e-12 of the interval takes it all */
         const int last = !(dt < (t1 - t) * (1.0 - 1e-12));
@@ -667,7 +669,7 @@ long orc_rkf45(int lmax, int n, const double *E, const double *U, double *c, int
         err = cc > 0.0 ? sqrt(ee / cc) : 0.0;
         ++att;
         const int ok = err <= tol;
-        if (ok || h <= dt_min) {
+        if (ok || h <= dt_min || dt <= dt_min) {
             if (!ok) ++forced;
             memcpy(c, x, sizeof(double) * 2 * N);
             if (kind == 0 && g_gauge == 1) A -= gl5(t, t + h, E0, om, ncyc);
@@ -681,12 +683,14 @@ long orc_rkf45(int lmax, int n, const double *E, const double *U, double *c, int
         double nd = h * fac;
         nd = nd < dt_min ? dt_min : (nd > dt_max ? dt_max : nd);
         dt = nd;
+        if (!(t + dt > t) && t < t1) { stalled = 1; break; }   /* no further progress possible */
     }
     free(k);
     free(x);
     stats[0] = acc;
     stats[1] = rej;
     stats[2] = forced;
+    stats[3] = stalled;
     tout[0] = t;
     tout[1] = dt;
     tout[2] = err;

@@ -18,6 +18,7 @@
 #include "plan.h"
 #include "tc.h"
 #include "lanczos.h"
+#include "rkf.h"
 
 using tdse::SysDesc;
 using tdse::Seg;
@@ -89,6 +90,8 @@ struct tdse_ctx {
     float umax_all = 0.f;              // max |U| over all blocks (float-float batched GEMM)
     // Lanczos: Krylov vectors, work vector, partial sums, scalars
     DevBuf lzV, lzw, lzparts, lzscal;
+    // RKF 4(5): stage derivatives k_1..k_5, the candidate state, partial sums, controller
+    DevBuf rkK, rkY, rkparts, rkctrl;
     // bf16x3 tensor-core path: dipole planes, energies as float-float, float-float
     // states, double-buffered bf16 state planes and their TMA descriptors
     DevBuf tU, tEdf, tc_c, tc_x, tc_acc, tc_planes, tc_fdf;
@@ -633,6 +636,100 @@ tdse_status tdse_propagate(tdse_ctx *ctx, double *c, const double *field, int sa
     if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
     return propagate_impl(ctx, c, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold,
                           (cudaStream_t)stream);
+}
+
+tdse_status tdse_propagate_rkf45(tdse_ctx *ctx, double *c, const tdse_field_fn *field, double t0, double t1,
+                                 double dt0, double tol, double dt_min, double dt_max, long max_attempts,
+                                 tdse_rkf_stats *stats, void *stream)
+{
+    g_err.clear();
+    if (!ctx || !c || !field) return fail(TDSE_EINVAL, "NULL argument");
+    if (!aligned16(c)) return fail(TDSE_EINVAL, "c must be 16-byte aligned");
+    if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
+    if (field->kind != TDSE_FIELD_SIN2 && field->kind != TDSE_FIELD_CONST) return fail(TDSE_EINVAL, "unknown field kind");
+    const double vals[] = {field->E0, field->omega, field->cycles, field->a0, t0, t1, dt0, tol, dt_min};
+    for (double v : vals)
+        if (!std::isfinite(v)) return fail(TDSE_EINVAL, "non-finite argument");
+    if (field->kind == TDSE_FIELD_SIN2 && !(field->omega > 0.0 && field->cycles > 0.0))
+        return fail(TDSE_EINVAL, "the sin^2 pulse needs omega > 0 and cycles > 0");
+    if (!(t1 >= t0)) return fail(TDSE_EINVAL, "need t1 >= t0");
+    if (!(dt0 > 0.0) || !(tol > 0.0)) return fail(TDSE_EINVAL, "need dt0 > 0 and tol > 0");
+    if (!(dt_min >= 0.0) || !(dt_max > 0.0) || dt_min > dt_max) return fail(TDSE_EINVAL, "need 0 <= dt_min <= dt_max, dt_max > 0");
+    if (max_attempts < 0) return fail(TDSE_EINVAL, "max_attempts must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = ctx->N;
+    const int nblk = (int)((N + 255) / 256);
+    CUDA_TRY(ctx->rkK.ensure(sizeof(double2) * 5 * (size_t)N));
+    CUDA_TRY(ctx->rkY.ensure(sizeof(double2) * (size_t)N));
+    CUDA_TRY(ctx->rkparts.ensure(sizeof(double) * 2 * (size_t)nblk));
+    CUDA_TRY(ctx->rkctrl.ensure(sizeof(tdse::RkfCtrl)));
+    SysDesc d = ctx->desc;
+    d.c = (double2 *)c;
+    d.field = nullptr;
+    tdse_status st = stage_desc(ctx, d, s);
+    if (st != TDSE_OK) return st;
+    tdse::RkfParams p{};
+    p.kind = field->kind;
+    p.gauge = ctx->desc.gauge;
+    p.E0 = field->E0;
+    p.om = field->kind == TDSE_FIELD_SIN2 ? field->omega : 1.0;
+    p.T = field->kind == TDSE_FIELD_SIN2 ? 2.0 * 3.14159265358979323846 * field->cycles / field->omega : 0.0;
+    p.t1 = t1;
+    p.tol = tol;
+    p.dt_min = dt_min;
+    p.dt_max = dt_max;
+    p.max_attempts = max_attempts;
+    const SysDesc *sys = ctx->sys.as<SysDesc>();
+    tdse::RkfCtrl *C = ctx->rkctrl.as<tdse::RkfCtrl>();
+    double2 *K = ctx->rkK.as<double2>(), *Y = ctx->rkY.as<double2>();
+    double *parts = ctx->rkparts.as<double>();
+    CUDA_TRY(tdse::rkf_launch_begin(C, p, t0, dt0, field->a0, s));
+    CUDA_TRY(tdse::rkf_launch_apply(ctx->prec, sys, N, C, Y, s));
+    ctx->launches += 2;
+    tdse::RkfCtrl h{};
+    long chunk = 4;
+    long long seen = -1;
+    for (;;) {
+        for (long q = 0; q < chunk; ++q) {
+            for (int stg = 0; stg < 6; ++stg) {
+                st = launch_product(ctx, 0, s);
+                if (st != TDSE_OK) return st;
+                CUDA_TRY(tdse::rkf_launch_stage(ctx->prec, sys, N, C, stg, K, Y, parts, s));
+            }
+            CUDA_TRY(tdse::rkf_launch_control(C, p, parts, nblk, s));
+            CUDA_TRY(tdse::rkf_launch_apply(ctx->prec, sys, N, C, Y, s));
+            ctx->launches += 8;
+        }
+        CUDA_TRY(cudaMemcpyAsync(&h, C, sizeof(h), cudaMemcpyDeviceToHost, s));
+        st = tdse_sync(ctx, stream);
+        if (st != TDSE_OK) return st;
+        if (h.stalled)
+            return fail(TDSE_EINVAL, "RKF step size underflow at t=%.17g: tol %.3g is not attainable (give dt_min > 0)",
+                        h.t, tol);
+        if (h.done) break;
+        if (h.attempts <= seen)
+            return fail(TDSE_ECUDA, "RKF controller made no progress (t=%.17g, attempts=%lld)", h.t, h.attempts);
+        seen = h.attempts;
+        // attempts still needed at the current step size, plus a margin for rejections
+        const double rem = (t1 - h.t) / (h.dt > 0.0 ? h.dt : 1.0);
+        double want = rem * 1.1 + 1.0;
+        const double left = (double)(max_attempts - h.attempts);
+        want = want < left ? want : left;
+        // grow geometrically: attempts launched after `done` are wasted products
+        const double cap = 2.0 * (double)h.attempts > 4.0 ? 2.0 * (double)h.attempts : 4.0;
+        want = want < cap ? want : cap;
+        chunk = want < 1.0 ? 1 : (want > 4096.0 ? 4096 : (long)want);
+    }
+    if (stats) {
+        stats->accepted = (long)h.accepted;
+        stats->rejected = (long)h.rejected;
+        stats->forced = (long)h.forced;
+        stats->t = h.t;
+        stats->dt = h.dt;
+        stats->err = h.err;
+        stats->a = h.A;
+    }
+    return TDSE_OK;
 }
 
 tdse_status tdse_propagate_host(tdse_ctx *ctx, double *c_host, const double *field_host, int samples_per_step,

@@ -7,35 +7,11 @@
 // every later sample adds one interval [t0 + (k-1) h, t0 + k h].  Interval
 // endpoints are computed from their index (no running sum of t).
 #include "kernels.h"
+#include "pulse.cuh"
 
 namespace tdse {
 
 namespace {
-
-struct Sin2 {
-    double E0, om, T;
-};
-
-__device__ __forceinline__ double sin2_field(const Sin2 &p, double t)
-{
-    if (t < 0.0 || t > p.T) return 0.0;
-    const double s = sin(3.14159265358979323846 * t / p.T);
-    return p.E0 * s * s * sin(p.om * t);
-}
-
-// integral of E over [a, b] by the 5-point Gauss-Legendre rule: nodes are the
-// roots of P_5, 0 and +-sqrt(5 -+ 2 sqrt(10/7))/3, weights 128/225 and
-// (322 +- 13 sqrt(70))/900
-__device__ double gauss5(const Sin2 &p, double a, double b)
-{
-    const double r = 2.0 * sqrt(10.0 / 7.0);
-    const double x1 = sqrt(5.0 - r) / 3.0, x2 = sqrt(5.0 + r) / 3.0;
-    const double w1 = (322.0 + 13.0 * sqrt(70.0)) / 900.0, w2 = (322.0 - 13.0 * sqrt(70.0)) / 900.0;
-    const double c = 0.5 * (a + b), h = 0.5 * (b - a);
-    const double s = (128.0 / 225.0) * sin2_field(p, c) + w1 * (sin2_field(p, c - h * x1) + sin2_field(p, c + h * x1)) +
-                     w2 * (sin2_field(p, c - h * x2) + sin2_field(p, c + h * x2));
-    return h * s;
-}
 
 // q[k] = -int over interval k (k >= 1)
 __global__ void vp_intervals(Sin2 p, double t0, double h, long long ns, double *__restrict__ q)

@@ -54,6 +54,19 @@ _SIGS = {
     "tdse_group_destroy": ([_vp], None),
     "tdse_group_propagate": ([_vp, _vp, _vp, _i, _d, _l, _vp], _i),
 }
+class _FieldFn(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("E0", ctypes.c_double), ("omega", ctypes.c_double),
+                ("cycles", ctypes.c_double), ("a0", ctypes.c_double)]
+
+
+class _RkfStats(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_long), ("rejected", ctypes.c_long), ("forced", ctypes.c_long),
+                ("t", ctypes.c_double), ("dt", ctypes.c_double), ("err", ctypes.c_double), ("a", ctypes.c_double)]
+
+
+FIELD_KINDS = {"sin2": 0, "const": 1}
+_SIGS["tdse_propagate_rkf45"] = ([_vp, _vp, ctypes.POINTER(_FieldFn), _d, _d, _d, _d, _d, _d, _l,
+                                  ctypes.POINTER(_RkfStats), _vp], _i)
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
@@ -152,6 +165,19 @@ class Hamiltonian:
     @property
     def handle(self):
         return self._h
+
+    def propagate_rkf45(self, c, t0, t1, dt0, tol, field="sin2", E0=0.0, omega=1.0, cycles=10, a0=0.0,
+                        dt_min=0.0, dt_max=float("inf"), max_attempts=10 ** 7, stream=None):
+        """Adaptive Runge-Kutta-Fehlberg 4(5) from t0 to t1 (synchronises the
+        stream).  Returns dict(accepted, rejected, forced, t, dt, err, A)."""
+        c = _dev_c(c, self.N)
+        fn = _FieldFn(FIELD_KINDS[field], float(E0), float(omega), float(cycles), float(a0))
+        st = _RkfStats()
+        _check(_lib.tdse_propagate_rkf45(self._h, _ptr(c), ctypes.byref(fn), float(t0), float(t1), float(dt0),
+                                         float(tol), float(dt_min), float(min(dt_max, 1e300)), int(max_attempts),
+                                         ctypes.byref(st), _stream(stream)))
+        return dict(accepted=st.accepted, rejected=st.rejected, forced=st.forced, t=st.t, dt=st.dt, err=st.err,
+                    A=st.a)
 
     def set_gauge(self, gauge):
         """"length" (f = E(t), D real symmetric) or "velocity" (f = A(t), D = i K)."""

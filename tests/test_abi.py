@@ -76,3 +76,10 @@ def test_gauge_argument_checks(lib):
     assert f(0.1, 0.5, 10, 0.0, 0.01, 0, buf, None) == 1                   # no samples
     assert f(0.1, 0.5, 10, 1e9, 1e-3, 8, buf, None) == 1                   # t0/h too large
     assert f(float("nan"), 0.5, 10, 0.0, 0.01, 8, buf, None) == 1
+
+
+def test_rkf45_argument_checks(lib):
+    f = lib.tdse_propagate_rkf45
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_double] * 6 + [ctypes.c_long] + [ctypes.c_void_p] * 2
+    assert f(None, None, None, 0.0, 1.0, 0.1, 1e-8, 0.0, 1.0, 10, None, None) == 1

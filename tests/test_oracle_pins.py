@@ -554,7 +554,7 @@ def test_rkf45_controller_matches_an_independent_simulation():
         h = t1 - t if last else dt
         R5, R4 = _rkf_polys(-1j * E * h)
         err = np.linalg.norm((R5 - R4) * cc) / np.linalg.norm(cc)
-        if err <= tol or h <= dtmin:
+        if err <= tol or h <= dtmin or dt <= dtmin:
             cc = R5 * cc
             t = t1 if last else t + h
             acc += 1
@@ -611,3 +611,18 @@ def test_rkf45_sin2_pulse_matches_an_independent_integrator(gauge):
     assert rel(c, ref) < 1e-9
     if gauge == "velocity":
         assert abs(info["A"] - _A_closed(T, E0, om, cyc)) < 1e-13
+
+
+def test_rkf45_forced_steps_and_stall():
+    """Steps pinned at dt_min are accepted (forced) and finish on t1 even when
+    rounding leaves the last remainder a hair above dt; with dt_min = 0 and an
+    unattainable tol the run stops as stalled instead of looping."""
+    lmax, n = 1, 8
+    E, U = rand_system(lmax, n, 88)
+    c0 = inputs.random_state((lmax + 1) * n, 89)
+    c, info = oracle.rkf45(lmax, n, E, U, c0, 0.0, 8.0, 0.05, 1e-30, field="const", E0=0.2,
+                           dt_min=0.05, dt_max=0.05)
+    assert info["t"] == 8.0 and info["accepted"] == info["forced"] == 160 and info["rejected"] == 0
+    c, info = oracle.rkf45(lmax, n, E, U, c0, 1.0, 2.0, 0.05, 1e-300, field="const", E0=0.2)
+    assert info["stalled"] and info["accepted"] == 0 and info["rejected"] < 100
+    assert np.array_equal(c, c0)
