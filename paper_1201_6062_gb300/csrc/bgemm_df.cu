@@ -12,8 +12,9 @@
 // T could not hold.  The low-order terms (uh xl, ul xh, that remainder) go to
 // L.  After each chunk (T - sigma) + L is added to a float-float running sum
 // (TwoSum), so the residual errors scale with one chunk's sigma, not with the
-// whole K = 2n sum.  6 FP32 instructions per product, ~0.3 per product for
-// the fold.
+// whole K = 2n sum.  6 FP32 operations per product (issued as 3 paired
+// FFMA2/FADD2 instructions, the Re and Im planes of a pulse in the two
+// lanes), ~0.3 per product for the fold.
 //
 // sigma is per output column (one pulse's real or imaginary plane), so that
 // pulses of very different magnitude keep their own relative accuracy.  The
@@ -41,14 +42,18 @@ __device__ __forceinline__ float pow2_above(float bound)
     return ldexpf(1.f, e > -100 ? e : -100);
 }
 
-__device__ __forceinline__ void acc_prod(float &T, float &L, float uh, float ul, float xh, float xl)
+// One product into two adjacent outputs (the Re and Im planes of a pulse)
+// with paired FP32 instructions (FFMA2/FADD2, each lane rounded as the scalar
+// operation).  Per lane: t = fl(T + uh xh); d = t - T (exact); r =
+// fma(uh, xh, -d); L += r; L = fma(uh, xl, L); L = fma(ul, xh, L); T = t.
+__device__ __forceinline__ void acc_prod2(float2 &T, float2 &L, float2 uh, float2 ul, float2 xh, float2 xl)
 {
-    const float t = __fmaf_rn(uh, xh, T);
-    const float d = __fsub_rn(t, T);
-    const float r = __fmaf_rn(uh, xh, -d);
-    float l = __fadd_rn(L, r);
-    l = __fmaf_rn(uh, xl, l);
-    L = __fmaf_rn(ul, xh, l);
+    const float2 t = __ffma2_rn(uh, xh, T);
+    const float2 d = __fadd2_rn(t, make_float2(-T.x, -T.y));
+    const float2 r = __ffma2_rn(uh, xh, make_float2(-d.x, -d.y));
+    float2 l = __fadd2_rn(L, r);
+    l = __ffma2_rn(uh, xl, l);
+    L = __ffma2_rn(ul, xh, l);
     T = t;
 }
 
@@ -60,6 +65,16 @@ __device__ __forceinline__ void fold(float &Rh, float &Rl, float &T, float &L, f
     Rl = __fadd_rn(Rl, __fadd_rn(s.l, L));
     T = sigma;
     L = 0.f;
+}
+
+__device__ __forceinline__ void fold2(float &Rh0, float &Rl0, float &Rh1, float &Rl1, float2 &T, float2 &L,
+                                      float s0, float s1)
+{
+    float t0 = T.x, t1 = T.y, l0 = L.x, l1 = L.y;
+    fold(Rh0, Rl0, t0, l0, s0);
+    fold(Rh1, Rl1, t1, l1, s1);
+    T = make_float2(t0, t1);
+    L = make_float2(l0, l1);
 }
 
 }  // namespace
@@ -93,11 +108,18 @@ bgemm_df_kernel(BatchArgs A)
         sigma[q] = pow2_above(4.f * (float)(BK * KC_TILES) * A.umax * xm);
     }
 
-    float T[4][4], L[4][4], Rh[4][4], Rl[4][4];
+    float2 T[4][2], L[4][2];
+    float Rh[4][4], Rl[4][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 4; ++r) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { T[r][q] = sigma[q]; L[r][q] = 0.f; Rh[r][q] = 0.f; Rl[r][q] = 0.f; }
+        for (int p = 0; p < 2; ++p) {
+            T[r][p] = make_float2(sigma[2 * p], sigma[2 * p + 1]);
+            L[r][p] = make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { Rh[r][q] = 0.f; Rl[r][q] = 0.f; }
+    }
 
     // loader roles: m (or c) = tid & 63, four consecutive k at kq*4
     const int lm = tid & 63, kq = tid >> 6;
@@ -146,18 +168,23 @@ bgemm_df_kernel(BatchArgs A)
                 const float4 bh = *reinterpret_cast<const float4 *>(&Bh[kk][tx * 4]);
                 const float4 bl = *reinterpret_cast<const float4 *>(&Bl[kk][tx * 4]);
                 const float a_h[4] = {ah.x, ah.y, ah.z, ah.w}, a_l[4] = {al.x, al.y, al.z, al.w};
-                const float b_h[4] = {bh.x, bh.y, bh.z, bh.w}, b_l[4] = {bl.x, bl.y, bl.z, bl.w};
+                const float2 b_h[2] = {make_float2(bh.x, bh.y), make_float2(bh.z, bh.w)};
+                const float2 b_l[2] = {make_float2(bl.x, bl.y), make_float2(bl.z, bl.w)};
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r) {
+                    const float2 uh = make_float2(a_h[r], a_h[r]), ul = make_float2(a_l[r], a_l[r]);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc_prod(T[r][q], L[r][q], a_h[r], a_l[r], b_h[q], b_l[q]);
+                    for (int p = 0; p < 2; ++p) acc_prod2(T[r][p], L[r][p], uh, ul, b_h[p], b_l[p]);
+                }
             }
             if (++tiles == KC_TILES) {
                 tiles = 0;
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) fold(Rh[r][q], Rl[r][q], T[r][q], L[r][q], sigma[q]);
+                    for (int p = 0; p < 2; ++p)
+                        fold2(Rh[r][2 * p], Rl[r][2 * p], Rh[r][2 * p + 1], Rl[r][2 * p + 1], T[r][p], L[r][p],
+                              sigma[2 * p], sigma[2 * p + 1]);
             }
         }
     }
@@ -165,7 +192,9 @@ bgemm_df_kernel(BatchArgs A)
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) fold(Rh[r][q], Rl[r][q], T[r][q], L[r][q], sigma[q]);
+            for (int p = 0; p < 2; ++p)
+                fold2(Rh[r][2 * p], Rl[r][2 * p], Rh[r][2 * p + 1], Rl[r][2 * p + 1], T[r][p], L[r][p],
+                      sigma[2 * p], sigma[2 * p + 1]);
     }
 
     // epilogue: columns 4tx..4tx+3 are (Re, Im) of pulses 2tx and 2tx+1 of the tile
