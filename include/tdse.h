@@ -367,9 +367,11 @@ tdse_status tdse_populations_noalloc(const double *c, const double *energies, in
                                      void *stream);
 
 /*
- * Uneven batches: several contexts of different (lmax, n) advanced together,
- * one kernel launch per stage for all of them (rows of every system are split
- * evenly over the GPU's SMs).  All contexts must share one precision.
+ * Uneven batches: several contexts of different (lmax, n) advanced together.
+ * The systems are bucketed by the thread layout their row length takes (a
+ * handful of classes); each stage is one block-product launch per bucket
+ * (the bucket's rows split evenly over the GPU's SMs) and one epilogue
+ * launch for all systems.  All contexts must share one precision.
  */
 typedef struct tdse_group tdse_group;
 
@@ -382,8 +384,8 @@ void tdse_group_destroy(tdse_group *g);
  * c_ptrs[s]      device, complex [N_s] state of system s (in/out).
  * field_ptrs[s]  device, FP64 [samples_per_step*nsteps + 1] field of system s.
  * Both arrays are host arrays of `count` device pointers.  RK4 only.  Each
- * stage is one block-product launch and one epilogue launch for all systems;
- * one step is captured once into a CUDA graph (re-captured when dt or
+ * stage is one block-product launch per bucket and one epilogue launch for
+ * all systems; one step is captured once into a CUDA graph (re-captured when dt or
  * samples_per_step change) and replayed nsteps times.  The systems' own
  * scratch vectors are used, so a context must not be propagated on its own
  * while its group runs.  Errors: EINVAL, ECUDA.
@@ -396,10 +398,12 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs,
 tdse_status tdse_group_sync(tdse_group *g, void *stream);
 
 /*
- * tdse_group_tune — autotuner: times `reps` block-product launches for every
- * valid ring-stage depth (1, 2, 4, 8 rows per bulk copy) on the group's own
- * plan and keeps the fastest for later tdse_group_propagate calls.  Reports
- * the choice and its time per launch (either pointer may be NULL).  Clobbers
+ * tdse_group_tune — autotuner: for each bucket, times `reps` block-product
+ * launches for every valid ring-stage depth (1, 2, 4, 8 rows per bulk copy)
+ * on the bucket's own plan and keeps the fastest for later
+ * tdse_group_propagate calls.  Reports the depth chosen for the bucket with
+ * the most dipole bytes and the summed best time of one product of every
+ * system (either pointer may be NULL).  Clobbers
  * the members' scratch vectors; synchronises `stream`.
  * Errors: EINVAL, ECUDA, ETIMEOUT.
  */

@@ -1,6 +1,7 @@
 // C ABI of the propagator (declarations and contracts in include/tdse.h).
 // Host orchestration only: argument checks, device storage, the work plan and
 // the launch sequence.  Every arithmetic step runs in the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -130,7 +131,7 @@ static int sm_count()
 
 // Build the mat-vec plan for the given systems and upload it.
 static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std::vector<int> &n, MvPlan &mp,
-                              tdse::Plan &plan)
+                              tdse::Plan &plan, const std::vector<int> *global_id = nullptr)
 {
     int nmax = 1;
     long long rows = 0, amps = 0;
@@ -153,13 +154,14 @@ static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std:
     std::vector<Seg> segs(plan.segs.size());
     for (size_t i = 0; i < segs.size(); ++i) {
         const tdse::PlanSeg &p = plan.segs[i];
-        segs[i] = Seg{p.sys, p.l, p.i0, p.i1, p.slot};
+        segs[i] = Seg{global_id ? (*global_id)[p.sys] : p.sys, p.l, p.i0, p.i1, p.slot};
     }
     std::vector<int2> blk;
     for (size_t s = 0; s < n.size(); ++s) {
         const long long N = (long long)(lmax[s] + 1) * n[s];
         amps += N;
-        for (long long a = 0; a < N; a += 256) blk.push_back(make_int2((int)s, (int)a));
+        const int id = global_id ? (*global_id)[s] : (int)s;
+        for (long long a = 0; a < N; a += 256) blk.push_back(make_int2(id, (int)a));
     }
     mp.nblk = (int)blk.size();
     CUDA_TRY(mp.segs.ensure(sizeof(Seg) * (segs.empty() ? 1 : segs.size())));
@@ -1154,10 +1156,19 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
     return TDSE_OK;
 }
 
+// Systems whose rows take the same thread layout share one product launch.
+struct GroupBucket {
+    std::vector<int> members;           // system indices in the group
+    long long bytes = 0;                // dipole bytes of one product
+    MvPlan plan;                        // work split over all SMs, layout for the bucket's largest n
+    int tuned_rs = 0;                   // rows per ring stage chosen by tdse_group_tune (0: default)
+};
+
 struct tdse_group {
     std::vector<tdse_ctx *> sys;
     int prec = 0;
-    MvPlan plan;
+    MvPlan plan;                        // epilogue / prep block map over all systems
+    std::vector<GroupBucket> buckets;   // one product launch each, back to back
     std::vector<DevBuf> P, sb;          // per-system column-partial slots and slot starts
     std::vector<SysDesc> desc;          // per-system descriptors (static fields filled)
     DevBuf ddesc;                       // device descriptor table
@@ -1167,7 +1178,6 @@ struct tdse_group {
     cudaEvent_t stage_ev = nullptr;
     bool stage_pending = false;
     long launches = 0;
-    int tuned_rs = 0;                   // rows per ring stage chosen by tdse_group_tune (0: default)
     // captured one-step graph (valid for graph_dt / graph_sps)
     cudaGraphExec_t gexec = nullptr;
     double graph_dt = 0.0;
@@ -1201,24 +1211,56 @@ tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **
     g->prec = systems[0]->prec;
     std::vector<int> lm(count), nn(count);
     for (int i = 0; i < count; ++i) { lm[i] = systems[i]->lmax; nn[i] = systems[i]->n; }
-    tdse::Plan plan;
-    tdse_status st = build_plan(g->prec, lm, nn, g->plan, plan);
+    // The epilogue and prep block map over all systems (its product plan is not used).
+    tdse::Plan all;
+    tdse_status st = build_plan(g->prec, lm, nn, g->plan, all);
     if (st != TDSE_OK) return bail(st);
+    // Bucket the systems by the thread layout each would take alone: a layout
+    // sized for the group's largest n leaves most threads idle on short rows,
+    // and its ring stage (rows of the longest stride) is tiny for them.
+    std::vector<int> key(count);
+    for (int i = 0; i < count; ++i) {
+        tdse::MvCfg c1{};
+        const int ld = (nn[i] + 3) & ~3;
+        if (tdse::mvt_config(g->prec, nn[i], ld, &c1)) key[i] = 100 + c1.idx;
+        else if (tdse::mv_config(g->prec, nn[i], &c1)) key[i] = c1.idx;
+        else return bail(fail(TDSE_ENOTSUP, "n=%d exceeds the supported maximum", nn[i]));
+    }
+    std::vector<int> keys(key);
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    g->buckets.resize(keys.size());
     g->P.resize(count);
     g->sb.resize(count);
     g->desc.resize(count);
-    for (int i = 0; i < count; ++i) {
-        tdse_ctx *c = systems[i];
-        const size_t ns = (size_t)(plan.nslots[i] > 0 ? plan.nslots[i] : 1);
-        cudaError_t e = g->P[i].ensure(sizeof(double2) * ns * c->n);
-        if (e == cudaSuccess) e = g->sb[i].ensure(sizeof(int) * (c->lmax + 1));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(g->sb[i].p, plan.sb[i].data(), sizeof(int) * (c->lmax + 1), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return bail(fail(TDSE_ECUDA, "group buffers: %s", cudaGetErrorString(e)));
-        SysDesc d = c->desc;
-        d.P = g->P[i].as<double2>();
-        d.sb = g->sb[i].as<int>();
-        g->desc[i] = d;
+    const int eb = elem_bytes(g->prec);
+    for (size_t b = 0; b < keys.size(); ++b) {
+        GroupBucket &bk = g->buckets[b];
+        std::vector<int> blm, bnn;
+        for (int i = 0; i < count; ++i)
+            if (key[i] == keys[b]) {
+                bk.members.push_back(i);
+                blm.push_back(lm[i]);
+                bnn.push_back(nn[i]);
+                bk.bytes += (long long)lm[i] * nn[i] * nn[i] * eb;
+            }
+        tdse::Plan plan;
+        st = build_plan(g->prec, blm, bnn, bk.plan, plan, &bk.members);
+        if (st != TDSE_OK) return bail(st);
+        for (size_t k = 0; k < bk.members.size(); ++k) {
+            const int i = bk.members[k];
+            tdse_ctx *c = systems[i];
+            const size_t ns = (size_t)(plan.nslots[k] > 0 ? plan.nslots[k] : 1);
+            cudaError_t e = g->P[i].ensure(sizeof(double2) * ns * c->n);
+            if (e == cudaSuccess) e = g->sb[i].ensure(sizeof(int) * (c->lmax + 1));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(g->sb[i].p, plan.sb[k].data(), sizeof(int) * (c->lmax + 1), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return bail(fail(TDSE_ECUDA, "group buffers: %s", cudaGetErrorString(e)));
+            SysDesc d = c->desc;
+            d.P = g->P[i].as<double2>();
+            d.sb = g->sb[i].as<int>();
+            g->desc[i] = d;
+        }
     }
     cudaError_t e = g->ddesc.ensure(sizeof(SysDesc) * count);
     if (e == cudaSuccess) e = g->errw.ensure(sizeof(int));
@@ -1233,30 +1275,46 @@ tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **
 
 void tdse_group_destroy(tdse_group *g) { delete g; }
 
-static tdse_status group_product(tdse_group *g, cudaStream_t s, const tdse::MvCfg &cfg)
+static tdse::MvCfg bucket_cfg(const GroupBucket &b)
 {
-    if (g->plan.grid <= 0) return TDSE_OK;
+    tdse::MvCfg cfg = b.plan.cfg;
+    if (cfg.tma && b.tuned_rs > 0) cfg.RS = b.tuned_rs;
+    return cfg;
+}
+
+static tdse_status bucket_product(tdse_group *g, const GroupBucket &b, const tdse::MvCfg &cfg, cudaStream_t s)
+{
+    if (b.plan.grid <= 0) return TDSE_OK;
     if (cfg.tma)
-        CUDA_TRY(tdse::launch_mvt(g->prec, cfg, g->plan.grid, g->ddesc.as<SysDesc>(), g->plan.segs.as<Seg>(),
-                                  g->plan.cta_off.as<int>(), g->errw.as<int>(), s));
+        CUDA_TRY(tdse::launch_mvt(g->prec, cfg, b.plan.grid, g->ddesc.as<SysDesc>(), b.plan.segs.as<Seg>(),
+                                  b.plan.cta_off.as<int>(), g->errw.as<int>(), s));
     else
-        CUDA_TRY(tdse::launch_mv(g->prec, cfg, g->plan.grid, g->ddesc.as<SysDesc>(), g->plan.segs.as<Seg>(),
-                                 g->plan.cta_off.as<int>(), s));
+        CUDA_TRY(tdse::launch_mv(g->prec, cfg, b.plan.grid, g->ddesc.as<SysDesc>(), b.plan.segs.as<Seg>(),
+                                 b.plan.cta_off.as<int>(), s));
     return TDSE_OK;
 }
 
-static tdse::MvCfg group_cfg(tdse_group *g)
+// One block product of every system: one launch per bucket.
+static tdse_status group_product(tdse_group *g, cudaStream_t s)
 {
-    tdse::MvCfg cfg = g->plan.cfg;
-    if (cfg.tma && g->tuned_rs > 0) cfg.RS = g->tuned_rs;
-    return cfg;
+    for (const GroupBucket &b : g->buckets) {
+        tdse_status st = bucket_product(g, b, bucket_cfg(b), s);
+        if (st != TDSE_OK) return st;
+    }
+    return TDSE_OK;
+}
+
+static int group_product_launches(const tdse_group *g)
+{
+    int k = 0;
+    for (const GroupBucket &b : g->buckets) k += b.plan.grid > 0;
+    return k;
 }
 
 // Enqueue one RK4 step (4 products + 4 epilogues + the step-counter bump);
 // the epilogues read the step index from g->kdev.
 static tdse_status group_step(tdse_group *g, int sps, double dt, cudaStream_t s)
 {
-    const tdse::MvCfg cfg = group_cfg(g);
     tdse::EpiArgs a{};
     a.mode = tdse::EPI_RK4;
     a.sps = sps;
@@ -1264,7 +1322,7 @@ static tdse_status group_step(tdse_group *g, int sps, double dt, cudaStream_t s)
     a.kdev = g->kdev.as<long long>();
     for (int q = 0; q < 4; ++q) {
         a.stage = q;
-        tdse_status st = group_product(g, s, cfg);
+        tdse_status st = group_product(g, s);
         if (st != TDSE_OK) return st;
         CUDA_TRY(tdse::launch_epi(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->ddesc.as<SysDesc>(), a, s));
     }
@@ -1301,8 +1359,10 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const dou
     // One step is captured once into a CUDA graph and replayed nsteps times.
     if (!g->gexec || g->graph_dt != dt || g->graph_sps != samples_per_step) {
         if (g->gexec) { cudaGraphExecDestroy(g->gexec); g->gexec = nullptr; }
-        const tdse::MvCfg cfg = group_cfg(g);
-        if (cfg.tma && g->plan.grid > 0) CUDA_TRY(tdse::mvt_prepare(g->prec, cfg));
+        for (const GroupBucket &b : g->buckets) {
+            const tdse::MvCfg cfg = bucket_cfg(b);
+            if (cfg.tma && b.plan.grid > 0) CUDA_TRY(tdse::mvt_prepare(g->prec, cfg));
+        }
         cudaStream_t cs;
         CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
@@ -1321,7 +1381,7 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const dou
         g->graph_sps = samples_per_step;
     }
     for (long k = 0; k < nsteps; ++k) CUDA_TRY(cudaGraphLaunch(g->gexec, s));
-    g->launches += 1 + nsteps * (4 * ((g->plan.grid > 0) + 1) + 1);
+    g->launches += 1 + nsteps * (4 * (group_product_launches(g) + 1) + 1);
     return TDSE_OK;
 }
 
@@ -1344,12 +1404,6 @@ tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *bes
     if (!g) return fail(TDSE_EINVAL, "NULL group");
     if (reps < 1) reps = 3;
     cudaStream_t s = (cudaStream_t)stream;
-    tdse::MvCfg base = g->plan.cfg;
-    if (!base.tma || g->plan.grid <= 0) {
-        if (chosen_rs) *chosen_rs = 0;
-        if (best_ms) *best_ms = 0.0;
-        return TDSE_OK;
-    }
     // The descriptors must point at valid state buffers: use each system's own scratch.
     if (g->stage_pending) CUDA_TRY(cudaEventSynchronize(g->stage_ev));
     const int count = (int)g->sys.size();
@@ -1365,31 +1419,43 @@ tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *bes
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    int best = base.RS;
-    double bestt = 1e300;
-    for (int rs = 1; rs <= 8; rs *= 2) {
-        tdse::MvCfg cfg = base;
-        if (!tdse::mvt_rs_valid(g->prec, cfg, rs, g->plan.max_ld)) continue;
-        cfg.RS = rs;
-        tdse_status st = group_product(g, s, cfg);          // warm-up
-        if (st != TDSE_OK) return st;
-        CUDA_TRY(cudaEventRecord(e0, s));
-        for (int r = 0; r < reps; ++r) {
-            st = group_product(g, s, cfg);
+    double total = 0.0;
+    int big_rs = 0;
+    long long big_bytes = -1;
+    // each bucket's launch is timed alone for every valid ring depth
+    for (GroupBucket &b : g->buckets) {
+        const tdse::MvCfg base = b.plan.cfg;
+        int best = base.RS;
+        double bestt = 1e300;
+        for (int rs = base.tma ? 1 : 0; rs <= (base.tma ? 8 : 0); rs = rs ? rs * 2 : 1) {
+            tdse::MvCfg cfg = base;
+            if (base.tma) {
+                if (!tdse::mvt_rs_valid(g->prec, cfg, rs, b.plan.max_ld)) continue;
+                cfg.RS = rs;
+            }
+            tdse_status st = bucket_product(g, b, cfg, s);          // warm-up
             if (st != TDSE_OK) return st;
+            CUDA_TRY(cudaEventRecord(e0, s));
+            for (int r = 0; r < reps; ++r) {
+                st = bucket_product(g, b, cfg, s);
+                if (st != TDSE_OK) return st;
+            }
+            CUDA_TRY(cudaEventRecord(e1, s));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms / reps < bestt) { bestt = ms / reps; best = rs; }
+            if (!base.tma) break;
         }
-        CUDA_TRY(cudaEventRecord(e1, s));
-        CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms / reps < bestt) { bestt = ms / reps; best = rs; }
+        b.tuned_rs = base.tma ? best : 0;
+        total += bestt;
+        if (b.bytes > big_bytes) { big_bytes = b.bytes; big_rs = b.tuned_rs; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    g->tuned_rs = best;
     if (g->gexec) { cudaGraphExecDestroy(g->gexec); g->gexec = nullptr; }
-    if (chosen_rs) *chosen_rs = best;
-    if (best_ms) *best_ms = bestt;
+    if (chosen_rs) *chosen_rs = big_rs;
+    if (best_ms) *best_ms = total;
     return tdse_group_sync(g, stream);
 }
 

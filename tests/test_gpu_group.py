@@ -71,3 +71,21 @@ def test_group_rejects_mixed_precision_and_duplicates(tdse_lib):
         tdse_lib.Group([a, b])
     with pytest.raises(tdse_lib.TDSEError):
         tdse_lib.Group([a, a])
+
+
+def test_group_members_keep_their_gauge(tdse_lib):
+    """Each member takes the gauge it had at group creation; products of
+    different layout buckets and gauges share the step."""
+    shapes = [(3, 600), (2, 90), (4, 1100)]
+    dt, nsteps = 0.02, 15
+    mem = members(shapes, dt, nsteps, seed0=300)
+    hams = [tdse_lib.Hamiltonian(E, U, lmax, n, "fp64") for (lmax, n, E, U, F, c0) in mem]
+    hams[1].set_gauge("velocity")
+    g = tdse_lib.Group(hams)
+    cs = [torch.from_numpy(m[5].copy()).cuda() for m in mem]
+    g.propagate(cs, [torch.from_numpy(m[4]).cuda() for m in mem], dt, nsteps)
+    g.sync()
+    for q, ((lmax, n, E, U, F, c0), c) in enumerate(zip(mem, cs)):
+        with oracle.gauge("velocity" if q == 1 else "length"):
+            ref, _ = oracle.rk4(lmax, n, E, U, c0, F, dt, nsteps)
+        assert rel(c.cpu().numpy(), ref) < 1e-10, q
