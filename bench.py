@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the batched pulse-sweep section")
     p.add_argument("--sweep-pulses", type=int, default=256)
+    p.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch (64 systems) section")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient section")
     p.add_argument("--accuracy-steps", type=int, default=2000,
                    help="steps of the error pass (the workload's 2000-step window; 0 skips it)")
     return p.parse_args()
@@ -287,6 +289,123 @@ def pulse_sweep_section(args):
     return out
 
 
+def uneven_section(args):
+    """64 systems of different (lmax, n) (lmax 4..32, n 200..1500, each its own
+    pulse) advanced together by tdse_group_propagate: RK4 amplitude-updates/s
+    with FP32 and float-float products after the ring-depth autotuner, the
+    product bandwidth, and the error against the oracle on the two smallest
+    members over the timed window."""
+    import torch
+    import oracle
+    from paper_1201_6062_gb300 import inputs, tdse
+    mem = inputs.uneven_batch(64)
+    dt, W, K = 0.01, 2, 10
+    t0 = 20.0
+    precs = ("fp32", "df32")
+    hams = {p: [] for p in precs}
+    elems = 0
+    small = sorted(range(len(mem)), key=lambda i: mem[i]["lmax"] * mem[i]["n"] ** 2)[:2]
+    keep = {}
+    for i, m in enumerate(mem):
+        E = inputs.energies(m["lmax"], m["n"])
+        U = inputs.dipoles(m["lmax"], m["n"], m["seed"])
+        elems += m["lmax"] * m["n"] ** 2
+        for p in precs:
+            hams[p].append(tdse.Hamiltonian(E, U, m["lmax"], m["n"], p))
+        if i in small:
+            keep[i] = (E, U)
+        del U
+    F = [inputs.field_samples(m["E0"], m["omega"], dt, W + K, 1, t0=t0) for m in mem]
+    C0 = [inputs.ground_state(m["lmax"], m["n"]) for m in mem]
+    amps = sum((m["lmax"] + 1) * m["n"] for m in mem)
+    out = {"workload": "uneven batch: 64 systems, lmax 4..32, n 200..1500 (default_rng(4)), %.3e dipole elements, "
+                       "RK4 dt=0.01, window t=20..20.12 a.u." % elems, "systems": len(mem), "amplitudes": amps}
+    for p in precs:
+        g = tdse.Group(hams[p])
+        rs, tune_ms = g.tune(3)
+        cs = [torch.from_numpy(c.copy()).cuda() for c in C0]
+        fw = [torch.from_numpy(f[:W + 1].copy()).cuda() for f in F]
+        ft = [torch.from_numpy(f[W:].copy()).cuda() for f in F]
+        g.propagate(cs, fw, dt, W)
+        g.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.propagate(cs, ft, dt, K)
+        e1.record()
+        e1.synchronize()
+        g.sync()
+        ms = e0.elapsed_time(e1) / K
+        err = 0.0
+        for i in small:
+            E, U = keep[i]
+            ref, _ = oracle.rk4(mem[i]["lmax"], mem[i]["n"], E, U, C0[i], F[i], dt, W + K)
+            err = max(err, float(np.linalg.norm(cs[i].cpu().numpy() - ref) / np.linalg.norm(ref)))
+        eb = 4 if p == "fp32" else 8
+        out[p] = {"value": amps / (ms / 1e3), "ms_per_step": ms, "product_gbs": 4 * elems * eb / (ms / 1e3) / 1e9,
+                  "tuned_rows_per_stage_largest_bucket": rs, "tuned_ms_per_product": tune_ms,
+                  "err_vs_oracle_max": err, "sampled_systems": small}
+        g.close()
+        for h in hams[p]:
+            h.close()
+        del cs
+        torch.cuda.empty_cache()
+    return out
+
+
+def adjoint_section(args):
+    """Gradient of the final bound-state population with respect to all 4096
+    field samples (lmax=15, n=500, dt=0.01, 4095 RK4 steps, FP64, checkpoints
+    every 64 steps): seconds per gradient, and central differences (h=1e-6)
+    on 8 samples from default_rng(5) computed with the same GPU propagator,
+    their error relative to the largest gradient entry (the difference
+    quotient's rounding, ~1e-16/h, is absolute)."""
+    import torch
+    from paper_1201_6062_gb300 import inputs, tdse
+    cfg = inputs.adjoint_system()
+    lmax, n, dt, T = cfg["lmax"], cfg["n"], cfg["dt"], cfg["nsteps"]
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, cfg["seed"])
+    F = inputs.adjoint_field(dt, T, cfg["E0"], cfg["omega"])
+    c0 = torch.from_numpy(inputs.ground_state(lmax, n)).cuda()
+    w = torch.from_numpy((E < 0).astype(np.float64)).cuda()
+    H = tdse.Hamiltonian(E, U, lmax, n, "fp64")
+    Fd = torch.from_numpy(F).cuda()
+    H.adjoint(c0, Fd, dt, T, w, checkpoint_every=64)            # warm-up
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g, cT, loss = H.adjoint(c0, Fd, dt, T, w, checkpoint_every=64)
+    e1.record()
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    g = g.cpu().numpy()
+
+    def fwd(Fx):
+        c = c0.clone()
+        H.propagate(c, torch.from_numpy(Fx).cuda(), dt, T)
+        return float(H.populations(c, per_state=False, per_l=False)["bound"].item())
+
+    idx = np.random.default_rng(5).choice(F.size, 8, replace=False)
+    h = 1e-6
+    errs = []
+    gmax = float(np.max(np.abs(g)))
+    for i in idx:
+        Fp, Fm = F.copy(), F.copy()
+        Fp[i] += h
+        Fm[i] -= h
+        fd = (fwd(Fp) - fwd(Fm)) / (2 * h)
+        errs.append(abs(fd - g[i]) / gmax)
+    H.close()
+    return {"workload": "adjoint lmax=15 n=500 (8000 amplitudes), 4095 RK4 steps, dt=0.01, 4096 field samples, "
+                        "loss = bound-state population, FP64, checkpoints every 64",
+            "seconds_per_gradient": sec, "loss": float(loss.item()),
+            "fd_samples": [int(i) for i in idx], "fd_err_max_rel_to_max_grad": float(max(errs)),
+            "max_abs_grad": gmax,
+            "products_per_step": "4 forward + 4 recompute + 4 reverse"}
+
+
 def run_ours(args):
     import torch
     from paper_1201_6062_gb300 import build
@@ -418,6 +537,14 @@ def run_ours(args):
     if rank == 0 and not args.no_sweep:
         sweep = pulse_sweep_section(args)
 
+    uneven = None
+    if rank == 0 and not args.no_uneven:
+        uneven = uneven_section(args)
+
+    adjoint = None
+    if rank == 0 and not args.no_adjoint:
+        adjoint = adjoint_section(args)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, args.cpu_seconds, E, U)
@@ -433,6 +560,8 @@ def run_ours(args):
             "gpu_launches": p["gpu_launches"],
             "variants": res,
             "pulse_sweep": sweep,
+            "uneven_batch": uneven,
+            "adjoint": adjoint,
         }
         print(json.dumps(line))
 
