@@ -128,7 +128,6 @@ __device__ __forceinline__ df df_neg(df a) { return df{-a.h, -a.l}; }
 
 struct dfc { df re, im; };
 
-__device__ __forceinline__ dfc ld_dfc(const float4 *p) { float4 v = *p; return dfc{df{v.x, v.y}, df{v.z, v.w}}; }
 __device__ __forceinline__ void st_dfc(float4 *p, dfc a) { *p = make_float4(a.re.h, a.re.l, a.im.h, a.im.l); }
 __device__ __forceinline__ dfc dfc_axpy(dfc c, df s, dfc k)   // c + s k
 {
@@ -142,13 +141,29 @@ __device__ __forceinline__ void split_bf16(df v, __nv_bfloat16 *h, __nv_bfloat16
     *l = __float2bfloat16_rn(__fadd_rn(__fsub_rn(v.h, __bfloat162float(hb)), v.l));
 }
 
+// The state values one (pulse, amplitude) update reads: the stage input,
+// c (RK4 stages after the first) and the accumulator.  Loaded for several
+// pulses before any of their updates stores, so the loads overlap instead of
+// each waiting behind the previous update's stores.
+struct TcIn { float4 x, c, acc; };
+
+__device__ __forceinline__ void tc_load(const TcArgs &A, long long q, bool rk4, bool from_c, TcIn &in)
+{
+    in.x = from_c ? A.c[q] : A.x[q];
+    if (rk4 && !from_c) in.c = A.c[q];
+    if (rk4 ? A.stage >= 1 : A.stage > 1) in.acc = A.acc[q];
+}
+
+__device__ __forceinline__ dfc as_dfc(float4 v) { return dfc{df{v.x, v.y}, df{v.z, v.w}}; }
+
 // One (pulse b, amplitude a) with D x = (dr, di): RK4 stage / Taylor term.
-__device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, df e, df f, float dr, float di)
+__device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, df e, df f, float dr, float di,
+                                          const TcIn &in)
 {
     const long long q = (long long)b * A.N + a;
     const bool rk4 = A.mode == 2;
     const bool from_c = rk4 ? (A.stage == 0) : (A.stage == 1);
-    const dfc xin = ld_dfc(from_c ? A.c + q : A.x + q);
+    const dfc xin = as_dfc(in.x);
     if (A.gauge) { const float t = dr; dr = -di; di = t; }
     // H x = E x + f D x ;  k = -i H x = (Im, -Re)
     const df hr = df_add(df_mul(e, xin.re), df_mulf(f, dr));
@@ -156,26 +171,26 @@ __device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, d
     const dfc k{hi, df_neg(hr)};
     dfc out;
     if (rk4) {
-        const dfc c = from_c ? xin : ld_dfc(A.c + q);
+        const dfc c = from_c ? xin : as_dfc(in.c);
         if (A.stage == 0) {
             st_dfc(A.acc + q, k);
             out = dfc_axpy(c, A.half_dt, k);
             st_dfc(A.x + q, out);
         } else if (A.stage < 3) {
-            const dfc ac = ld_dfc(A.acc + q);
+            const dfc ac = as_dfc(in.acc);
             const df two{2.f, 0.f};
             st_dfc(A.acc + q, dfc{df_add(ac.re, df_mul(two, k.re)), df_add(ac.im, df_mul(two, k.im))});
             out = dfc_axpy(c, A.stage == 1 ? A.half_dt : A.full_dt, k);
             st_dfc(A.x + q, out);
         } else {
-            const dfc ac = ld_dfc(A.acc + q);
+            const dfc ac = as_dfc(in.acc);
             const dfc s{df_add(ac.re, k.re), df_add(ac.im, k.im)};
             out = dfc_axpy(c, A.sixth_dt, s);
             st_dfc(A.c + q, out);
         }
     } else {
         const dfc T{df_mul(A.term_dt, k.re), df_mul(A.term_dt, k.im)};
-        const dfc base = (A.stage == 1) ? xin : ld_dfc(A.acc + q);
+        const dfc base = (A.stage == 1) ? xin : as_dfc(in.acc);
         const dfc sum{df_add(base.re, T.re), df_add(base.im, T.im)};
         if (A.stage < A.order) {
             st_dfc(A.acc + q, sum);
@@ -198,6 +213,7 @@ __device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, d
 // Two accumulators of TBN columns live in tensor memory, so the epilogue of
 // one tile runs while the products of the next are issued.
 constexpr int EPI_WARPS = 8;                       // 2 per TMEM lane quarter
+constexpr int TC_LOAD_GROUP = 8;                   // pulses whose state loads are issued together
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA issuer, epilogue
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -338,13 +354,25 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
                     for (int q = 0; q < 32; ++q) v[q] = 0.f;
                 }
                 if (valid_row) {
+                    const bool rk4 = A.mode == 2;
+                    const bool from_c = rk4 ? (A.stage == 0) : (A.stage == 1);
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int pb = chunk * 16 + jj;        // pulse within the tile
-                        const int b = c0 / 2 + pb;
-                        if (b < A.B) {
-                            const float2 fv = A.fdf[b];
-                            tc_update(A, b, a, e, df{fv.x, fv.y}, v[2 * jj], v[2 * jj + 1]);
+                    for (int g = 0; g < 16; g += TC_LOAD_GROUP) {
+                        TcIn in[TC_LOAD_GROUP];
+                        float2 fv[TC_LOAD_GROUP];
+#pragma unroll
+                        for (int u = 0; u < TC_LOAD_GROUP; ++u) {
+                            const int b = c0 / 2 + chunk * 16 + g + u;     // pulse
+                            if (b < A.B) {
+                                tc_load(A, (long long)b * A.N + a, rk4, from_c, in[u]);
+                                fv[u] = __ldg(A.fdf + b);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < TC_LOAD_GROUP; ++u) {
+                            const int jj = g + u;
+                            const int b = c0 / 2 + chunk * 16 + jj;
+                            if (b < A.B) tc_update(A, b, a, e, df{fv[u].x, fv[u].y}, v[2 * jj], v[2 * jj + 1], in[u]);
                         }
                     }
                 }
