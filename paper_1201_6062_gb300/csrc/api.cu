@@ -277,7 +277,7 @@ static tdse_status propagate_batch_tc(tdse_ctx *ctx, double *c, const double *fi
         __nv_bfloat16 *base = ctx->tc_planes.as<__nv_bfloat16>();
         const cuuint64_t dims[2] = {(cuuint64_t)plane, (cuuint64_t)(2 * B)};
         const cuuint64_t strides[1] = {(cuuint64_t)plane * 2};
-        const cuuint32_t box[2] = {64, 256};
+        const cuuint32_t box[2] = {64, (cuuint32_t)tdse::TC_TBN};
         for (int b = 0; b < 2; ++b) {
             tdse_status st = make_map(&ctx->tc_maps[b].Xh, base + (size_t)(2 * b) * 2 * B * plane, 2, dims, strides, box);
             if (st == TDSE_OK)

@@ -4,9 +4,10 @@
 // all pulses at once) with bf16x3 split precision: U = Uh + Ul and
 // X = Xh + Xl in bf16, and D = Uh Xh + Uh Xl + Ul Xh accumulated in FP32 in
 // tensor memory.  The transposed blocks U_l^T are stored explicitly, so both
-// products read K-major tiles.  Per CTA: one 128 x 256 output tile (128 rows
-// of block l, 128 pulses as re/im column pairs), warp 0 streams K tiles of A
-// and B with TMA into a 2-stage ring, one thread of warp 1 issues
+// products read K-major tiles.  Per CTA tile: 128 x 128 outputs (128 rows of
+// block l, 64 pulses as re/im column pairs; small tiles give every CTA
+// several tiles, so one tile's epilogue overlaps the next tile's products),
+// warp 0 streams K tiles of A and B with TMA into a 3-stage ring, one thread of warp 1 issues
 // tcgen05.mma, warps 2..5 read the accumulator with tcgen05.ld and apply the
 // RK4 stage / Taylor term update.  The batched state is float-float
 // (FP32 hi + lo, about 44 bits): the GB300 FP64 pipe is 1/64 of the FP32
@@ -20,10 +21,10 @@
 
 namespace tdse {
 
-constexpr int TBM = 128, TBN = 256, TBK = 64, TST = 2;
+constexpr int TBM = 128, TBN = TC_TBN, TBK = 64, TST = 3;
 constexpr int A_BYTES = TBM * TBK * 2;                  // 16 KB
-constexpr int B_BYTES = TBN * TBK * 2;                  // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB
+constexpr int B_BYTES = TBN * TBK * 2;                  // 16 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 64 KB
 constexpr int TC_SMEM = TST * STAGE_BYTES + 1024;       // + alignment slack
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;
 

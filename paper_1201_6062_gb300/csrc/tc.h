@@ -13,6 +13,10 @@ struct TcMaps {
     CUtensorMap Uh, Ul, Th, Tl, Xh, Xl;
 };
 
+// Output tile columns (pulse planes) per CTA tile; also the row count of the
+// state-plane TMA box.
+constexpr int TC_TBN = 128;
+
 struct TcArgs {
     int n, lmax, B, nb;
     long long N;            // amplitudes per pulse
