@@ -18,8 +18,8 @@
 namespace tdse {
 
 constexpr int RBT = 8;                 // rows per row-sum reduction chunk
-constexpr int NS = 6;                  // ring stages
-constexpr int STAGE_MAX = 32768;       // bytes of dipole rows per stage
+constexpr int NS = 3;                  // ring stages
+constexpr int STAGE_MAX = 65536;       // bytes of dipole rows per stage
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
 
 template <class P, int CT, int MAXG, int RS>
