@@ -144,7 +144,7 @@ struct PolF64 {
     static __device__ __forceinline__ Comp rdone(RowAcc a, Sigma) { return a; }
     template <int K> static __device__ __forceinline__ Sigma sigma(const XV *, float) { return 0; }
     // Column sums: per-chunk partials folded into the running sum.
-    static __device__ __forceinline__ Sigma csigma(float, float) { return 0; }
+    template <int K> static __device__ __forceinline__ Sigma csigma(float, float) { return 0; }
     static __device__ __forceinline__ float xabs(const XV &x) { return fmaxf(fabsf((float)x.re), fabsf((float)x.im)); }
     static __device__ __forceinline__ void cfold(Comp &run, RowAcc &a, Sigma)
     {
@@ -201,7 +201,7 @@ struct PolF32 {
     static __device__ __forceinline__ Comp rdone(RowAcc a, Sigma) { return a; }
     template <int K> static __device__ __forceinline__ Sigma sigma(const XV *, float) { return 0; }
     // Column sums: per-chunk partials folded into the running sum.
-    static __device__ __forceinline__ Sigma csigma(float, float) { return 0; }
+    template <int K> static __device__ __forceinline__ Sigma csigma(float, float) { return 0; }
     static __device__ __forceinline__ float xabs(const XV &x) { return fmaxf(fabsf((float)x.re), fabsf((float)x.im)); }
     static __device__ __forceinline__ void cfold(Comp &run, RowAcc &a, Sigma)
     {
@@ -275,9 +275,9 @@ struct PolDF32 {
     static __device__ __forceinline__ Comp rdone(RowAcc a, Sigma s) { return df{__fsub_rn(a.T, s), a.L}; }
     // Column sums over at most K rows with |x| <= xmax: the same offset
     // accumulator, folded into a float-float running sum after each chunk.
-    static __device__ __forceinline__ Sigma csigma(float xmax, float umax)
+    template <int K> static __device__ __forceinline__ Sigma csigma(float xmax, float umax)
     {
-        const float bound = 4.f * 8.f * umax * xmax;
+        const float bound = 4.f * (float)K * umax * xmax;
         if (!(bound > 0.f)) return 0x1p-100f;
         int e;
         frexpf(bound, &e);

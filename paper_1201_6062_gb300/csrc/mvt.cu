@@ -17,7 +17,8 @@
 
 namespace tdse {
 
-constexpr int RBT = 8;                 // rows per row-sum reduction chunk
+constexpr int RBT = 16;                // rows per row-sum reduction chunk (and column-sum fold)
+constexpr int RS_MAX = 8;              // rows per ring stage: 1, 2, 4 or 8
 constexpr int NS = 3;                  // ring stages
 constexpr int STAGE_MAX = 65536;       // bytes of dipole rows per stage
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
@@ -140,7 +141,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                 for (int w = 0; w < NW; ++w) xm = fmaxf(xm, xmax_sh[w]);
                 named_sync(1, CT);
             }
-            const typename P::Sigma csig = P::csigma(xm, um);
+            const typename P::Sigma csig = P::template csigma<RBT>(xm, um);
             typename P::RowAcc cpr[MAXG][CW], cpi[MAXG][CW];
 #pragma unroll
             for (int g = 0; g < MAXG; ++g)
@@ -324,7 +325,7 @@ bool mvt_config(int prec, int n, int ld, MvCfg *out)
     const long long rowbytes = (long long)ld * elem_size(prec);
     if (rowbytes > STAGE_MAX) return false;
     int rs = 1;
-    while (rs * 2 <= RBT && rs * 2 * rowbytes <= STAGE_MAX) rs *= 2;
+    while (rs * 2 <= RS_MAX && rs * 2 * rowbytes <= STAGE_MAX) rs *= 2;
     for (int i = 0; i < kNumTCfg; ++i) {
         if (groups <= kTCfg[i].CT * kTCfg[i].MAXG) {
             *out = MvCfg{i, kTCfg[i].CT, 1, kTCfg[i].MAXG, kTCfg[i].CT + 32};
