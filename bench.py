@@ -399,9 +399,22 @@ def adjoint_section(args):
         fd = (fwd(Fp) - fwd(Fm)) / (2 * h)
         errs.append(abs(fd - g[i]) / gmax)
     H.close()
+    # the same gradient with float-float products (FP64-class accuracy)
+    Hd = tdse.Hamiltonian(E, U, lmax, n, "df32")
+    Hd.adjoint(c0, Fd, dt, T, w, checkpoint_every=64)
+    torch.cuda.synchronize()
+    e0.record()
+    gd, _, _ = Hd.adjoint(c0, Fd, dt, T, w, checkpoint_every=64)
+    e1.record()
+    e1.synchronize()
+    sec_df = e0.elapsed_time(e1) / 1e3
+    gd = gd.cpu().numpy()
+    Hd.close()
     return {"workload": "adjoint lmax=15 n=500 (8000 amplitudes), 4095 RK4 steps, dt=0.01, 4096 field samples, "
                         "loss = bound-state population, FP64, checkpoints every 64",
             "seconds_per_gradient": sec, "loss": float(loss.item()),
+            "df32_seconds_per_gradient": sec_df,
+            "df32_grad_rel_diff_vs_fp64": float(np.linalg.norm(gd - g) / np.linalg.norm(g)),
             "fd_samples": [int(i) for i in idx], "fd_err_max_rel_to_max_grad": float(max(errs)),
             "max_abs_grad": gmax,
             "products_per_step": "4 forward + 4 recompute + 4 reverse"}
