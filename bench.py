@@ -155,6 +155,24 @@ def dist_setup(args):
     return None, 0, 1, 0
 
 
+def max_over_ranks(dist, ms, device=None):
+    """The slowest rank's time: every rank contributes its own timed-region
+    milliseconds and all receive the maximum (replicas only: no data-path
+    collective, this is the one reduction of the measurement)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world_size, units_per_rank, ms):
+    """Units of all ranks (each rank advances its own replica) per second of
+    the slowest rank."""
+    return world_size * units_per_rank / (ms / 1e3)
+
+
 def cpu_baseline(cfg, seconds, E=None, U=None):
     """The oracle as it stands on the host cores: RK4 steps of the same system
     until `seconds` have elapsed (at least one step)."""
@@ -467,11 +485,7 @@ def run_ours(args):
             dist.barrier()
         if sampler:
             clocks = sampler.stop()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
         _, _, launches = H.profile_read()
         # Same K steps again with every block-product launch bracketed by CUDA
         # events on the library's stream: the per-launch time of the dominant kernel.
@@ -486,7 +500,7 @@ def run_ours(args):
         alg_bytes = lmax * n * n * ub + N * (xb + 16)
         mv_avg = mv_ms / max(mv_n, 1)
         res[prec] = {
-            "value": ws * N * K / (ms / 1e3), "ms_per_step": ms / K, "mv_ms_avg": mv_avg,
+            "value": whole_job_rate(ws, N * K, ms), "ms_per_step": ms / K, "mv_ms_avg": mv_avg,
             "mv_launches": mv_n, "gpu_launches": launches,
             "mv_gbs": alg_bytes / (mv_avg / 1e3) / 1e9,
             "mv_tflops": 8.0 * lmax * n * n / (mv_avg / 1e3) / 1e12,
