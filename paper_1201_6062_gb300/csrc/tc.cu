@@ -8,8 +8,9 @@
 // block l, 64 pulses as re/im column pairs; small tiles give every CTA
 // several tiles, so one tile's epilogue overlaps the next tile's products),
 // warp 0 streams K tiles of A and B with TMA into a 3-stage ring, one thread of warp 1 issues
-// tcgen05.mma, warps 2..5 read the accumulator with tcgen05.ld and apply the
-// RK4 stage / Taylor term update.  The batched state is float-float
+// tcgen05.mma, warps 2..17 read the accumulator with tcgen05.ld and apply
+// the RK4 stage / Taylor term update (the update is bound by the latency of
+// its state loads, so it gets as many warps as the register file allows).  The batched state is float-float
 // (FP32 hi + lo, about 44 bits): the GB300 FP64 pipe is 1/64 of the FP32
 // pipe, and an FP64 state update would cost more than the products.
 // All waits are bounded (sync.cuh).
@@ -213,8 +214,10 @@ __device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, d
 // Persistent: each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // Two accumulators of TBN columns live in tensor memory, so the epilogue of
 // one tile runs while the products of the next are issued.
-constexpr int EPI_WARPS = 8;                       // 2 per TMEM lane quarter
-constexpr int TC_LOAD_GROUP = 8;                   // pulses whose state loads are issued together
+constexpr int EPI_WARPS = 16;                       // a multiple of 4: EPI_WARPS / 4 per TMEM lane quarter
+constexpr int EPI_CPW = (TBN / 32) / (EPI_WARPS / 4); // 32-column accumulator chunks per epilogue warp
+static_assert(EPI_CPW * (EPI_WARPS / 4) * 32 == TBN, "epilogue warps must split the tile's columns evenly");
+constexpr int TC_LOAD_GROUP = 2;                   // pulses whose state loads are issued together
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA issuer, epilogue
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -327,9 +330,9 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
             }
         }
     } else {
-        // ------------------------------------------- epilogue: warps 2..9
+        // ------------------------------------------ epilogue: warps 2..17
         const int quarter = warp & 3;                    // TMEM lanes this warp may read
-        const int half = (warp - 2) >> 2;                // which half of the TBN columns
+        const int part = (warp - 2) >> 2;                // which EPI_CPW chunks of the TBN columns
         int j = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
             const int l = t / (mt * nt), rem = t % (mt * nt);
@@ -346,7 +349,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
             df e{0.f, 0.f};
             if (valid_row) { const float2 ev = A.Edf[a]; e = df{ev.x, ev.y}; }
 #pragma unroll 1
-            for (int chunk = half * (TBN / 64); chunk < (half + 1) * (TBN / 64); ++chunk) {
+            for (int chunk = part * EPI_CPW; chunk < (part + 1) * EPI_CPW; ++chunk) {
                 float v[32];
                 if (T > 0) {
                     tmem_ld32(tmem + (uint32_t)(ab * TBN) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(chunk * 32), v);
