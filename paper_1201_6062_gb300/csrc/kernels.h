@@ -25,7 +25,7 @@ cudaError_t launch_pdl(const void *fn, dim3 grid, dim3 block, size_t smem, cudaS
 bool mv_config(int prec, int n, MvCfg *out);
 int mv_ctas_per_sm(int prec, const MvCfg &cfg);
 
-// Ring-fed variant for rows of more than 128 column groups; false if n/ld do
+// Ring-fed variant for rows of more than 32 column groups; false if n/ld do
 // not qualify.
 bool mvt_config(int prec, int n, int ld, MvCfg *out);
 // Sets the kernel attributes a launch needs (call outside stream capture).

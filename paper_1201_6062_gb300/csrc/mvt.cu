@@ -276,7 +276,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
 // ------------------------------------------------------ instantiations --
 // (CT, MAXG) thread layouts; RS in {1, 2, 4, 8} rows per stage.
 struct TCfg { int CT, MAXG; };
-static const TCfg kTCfg[] = {{256, 1}, {256, 2}, {256, 3}, {256, 4}, {512, 4}};
+static const TCfg kTCfg[] = {{128, 1}, {256, 1}, {256, 2}, {256, 3}, {256, 4}, {512, 4}};
 constexpr int kNumTCfg = sizeof(kTCfg) / sizeof(kTCfg[0]);
 
 template <class P, int CT, int MAXG>
@@ -295,11 +295,12 @@ template <class P>
 static const void *mvt_fn(int idx, int rs)
 {
     switch (idx) {
-    case 0: return mvt_fn_rs<P, 256, 1>(rs);
-    case 1: return mvt_fn_rs<P, 256, 2>(rs);
-    case 2: return mvt_fn_rs<P, 256, 3>(rs);
-    case 3: return mvt_fn_rs<P, 256, 4>(rs);
-    case 4: return rs <= 2 ? mvt_fn_rs<P, 512, 4>(rs) : nullptr;
+    case 0: return mvt_fn_rs<P, 128, 1>(rs);
+    case 1: return mvt_fn_rs<P, 256, 1>(rs);
+    case 2: return mvt_fn_rs<P, 256, 2>(rs);
+    case 3: return mvt_fn_rs<P, 256, 3>(rs);
+    case 4: return mvt_fn_rs<P, 256, 4>(rs);
+    case 5: return rs <= 2 ? mvt_fn_rs<P, 512, 4>(rs) : nullptr;
     }
     return nullptr;
 }
@@ -321,7 +322,7 @@ bool mvt_config(int prec, int n, int ld, MvCfg *out)
 {
     if (prec < 0 || prec > 2) return false;
     const int groups = (n + col_width(prec) - 1) / col_width(prec);
-    if (groups <= 128) return false;                       // small rows: per-thread loads (mv.cu)
+    if (groups <= 32) return false;                        // very short rows: per-thread loads (mv.cu)
     const long long rowbytes = (long long)ld * elem_size(prec);
     if (rowbytes > STAGE_MAX) return false;
     int rs = 1;

@@ -70,7 +70,8 @@ def test_hamiltonian_product_and_minus_i(tdse_lib, prec):
     ref = oracle.hmatvec(lmax, n, E, U, f, x)
     y = H.hmatvec(to_dev(x), f).cpu().numpy()
     ym = H.hmatvec(to_dev(x), f, minus_i=True).cpu().numpy()
-    tol = 1e-14 if prec != "fp32" else 1e-6
+    # H x is dominated by the exact diagonal; the float-float D x keeps ~44 bits
+    tol = {"fp64": 1e-14, "df32": 1e-12, "fp32": 1e-6}[prec]
     assert rel(y, ref) < tol
     assert rel(ym, -1j * ref) < tol
 
