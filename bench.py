@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-sweep", action="store_true", help="skip the batched pulse-sweep section")
     p.add_argument("--sweep-pulses", type=int, default=256)
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch (64 systems) section")
+    p.add_argument("--no-small", action="store_true", help="skip the small-system section")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient section")
     p.add_argument("--accuracy-steps", type=int, default=2000,
                    help="steps of the error pass (the workload's 2000-step window; 0 skips it)")
@@ -304,6 +305,47 @@ def pulse_sweep_section(args):
     out["speedup_bf16x3_vs_single_fp32"] = out["bf16x3"]["value"] / out["single_fp32"]["value"]
     out["speedup_df32_batched_vs_single_df32"] = out["df32"]["value"] / out["single_df32"]["value"]
     out["speedup_df32_batched_vs_single_fp64"] = out["df32"]["value"] / out["single_fp64"]["value"]
+    return out
+
+
+def small_section(args):
+    """The small system (lmax=3, n=50, 200 amplitudes, FP64 RK4, dt=0.02, the
+    whole 10-cycle pulse: 6284 steps): microseconds per step through
+    tdse_propagate and through a one-member group (the step replayed as a
+    CUDA graph), and the error of the final state against the oracle."""
+    import torch
+    import oracle
+    from paper_1201_6062_gb300 import inputs, tdse
+    cfg = inputs.small_system()
+    lmax, n, dt, T = cfg["lmax"], cfg["n"], cfg["dt"], cfg["nsteps"]
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, cfg["seed"])
+    F = inputs.field_samples(cfg["E0"], cfg["omega"], dt, T, 1)
+    c0 = inputs.ground_state(lmax, n)
+    ref, _ = oracle.rk4(lmax, n, E, U, c0, F, dt, T)
+    H = tdse.Hamiltonian(E, U, lmax, n, "fp64")
+    Fd = torch.from_numpy(F).cuda()
+    out = {"workload": "small system lmax=3 n=50 (200 amplitudes), FP64 RK4, dt=0.02, %d steps (whole pulse)" % T}
+    for how in ("propagate", "group_graph"):
+        g = tdse.Group([H]) if how == "group_graph" else None
+        c = torch.from_numpy(c0.copy()).cuda()
+        (g.propagate([c], [Fd], dt, T) if g else H.propagate(c, Fd, dt, T))     # warm-up
+        torch.cuda.synchronize()
+        c = torch.from_numpy(c0.copy()).cuda()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        (g.propagate([c], [Fd], dt, T) if g else H.propagate(c, Fd, dt, T))
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        got = c.cpu().numpy()
+        out[how] = {"us_per_step": ms * 1e3 / T, "value": 200 * T / (ms / 1e3),
+                    "err_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                    "norm_drift": float(abs(np.vdot(got, got).real - 1.0))}
+        if g:
+            g.close()
+    H.close()
     return out
 
 
@@ -565,6 +607,10 @@ def run_ours(args):
     if rank == 0 and not args.no_sweep:
         sweep = pulse_sweep_section(args)
 
+    small = None
+    if rank == 0 and not args.no_small:
+        small = small_section(args)
+
     uneven = None
     if rank == 0 and not args.no_uneven:
         uneven = uneven_section(args)
@@ -588,6 +634,7 @@ def run_ours(args):
             "gpu_launches": p["gpu_launches"],
             "variants": res,
             "pulse_sweep": sweep,
+            "small_system": small,
             "uneven_batch": uneven,
             "adjoint": adjoint,
         }

@@ -276,7 +276,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
 // ------------------------------------------------------ instantiations --
 // (CT, MAXG) thread layouts; RS in {1, 2, 4, 8} rows per stage.
 struct TCfg { int CT, MAXG; };
-static const TCfg kTCfg[] = {{128, 1}, {256, 1}, {256, 2}, {256, 3}, {256, 4}, {512, 4}};
+static const TCfg kTCfg[] = {{128, 1}, {128, 2}, {256, 2}, {256, 3}, {256, 4}, {512, 4}};
 constexpr int kNumTCfg = sizeof(kTCfg) / sizeof(kTCfg[0]);
 
 template <class P, int CT, int MAXG>
@@ -296,7 +296,7 @@ static const void *mvt_fn(int idx, int rs)
 {
     switch (idx) {
     case 0: return mvt_fn_rs<P, 128, 1>(rs);
-    case 1: return mvt_fn_rs<P, 256, 1>(rs);
+    case 1: return mvt_fn_rs<P, 128, 2>(rs);
     case 2: return mvt_fn_rs<P, 256, 2>(rs);
     case 3: return mvt_fn_rs<P, 256, 3>(rs);
     case 4: return mvt_fn_rs<P, 256, 4>(rs);
