@@ -137,6 +137,10 @@ tdse_status tdse_hmatvec(tdse_ctx *ctx, double f, const double *x, double *y,
  *   scheme          TDSE_RK4 or TDSE_TAYLOR.
  *   taylor_order    K >= 1 (Taylor only; ignored for RK4).
  *   taylor_hold     tdse_hold (Taylor only).
+ * Systems whose dipole blocks fit in one CTA's shared memory (at most 1024
+ * amplitudes; FP64 also lmax*n^2 <= 16384) run every step in a single
+ * launch of one CTA; larger ones take a product launch and an update launch
+ * per stage.  Block-product tracing (tdse_profile_*) sees only the latter.
  * Scratch vectors live in the context.  Asynchronous on `stream`; the
  * context must not be used on another stream concurrently.
  * Errors: EINVAL, ECUDA.

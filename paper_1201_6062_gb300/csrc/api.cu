@@ -601,6 +601,29 @@ static tdse_status propagate_impl(tdse_ctx *ctx, double *c, const double *field,
     if (st != TDSE_OK) return st;
     if (nsteps == 0) return TDSE_OK;
     if (scheme == TDSE_LANCZOS) return propagate_lanczos(ctx, c, sps, dt, nsteps, order, hold, s);
+    if (tdse::small_fits(ctx->prec, ctx->lmax, ctx->n, ctx->ld, ctx->N)) {
+        // the whole system fits in one CTA's shared memory: one launch for all steps
+        tdse::SmallArgs A{};
+        A.U = ctx->U.p;
+        A.bstride = ctx->bstride;
+        A.ld = ctx->ld;
+        A.n = ctx->n;
+        A.lmax = ctx->lmax;
+        A.N = ctx->N;
+        A.E = ctx->E.as<double>();
+        A.c = (double2 *)c;
+        A.field = field;
+        A.sps = sps;
+        A.mode = scheme == TDSE_RK4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
+        A.order = order;
+        A.hold = hold;
+        A.gauge = ctx->desc.gauge;
+        A.nsteps = nsteps;
+        A.dt = dt;
+        CUDA_TRY(tdse::launch_small(ctx->prec, A, s));
+        ctx->launches += 1;
+        return TDSE_OK;
+    }
     CUDA_TRY(tdse::launch_prep(ctx->prec, ctx->plan.nblk, ctx->plan.blk.as<int2>(), ctx->sys.as<SysDesc>(), 0, s));
     ctx->launches += 1;
     tdse::EpiArgs a{};

@@ -114,4 +114,21 @@ cudaError_t launch_pop_totals(const double *part, int L, int B, double *norm,
 cudaError_t launch_vector_potential_sin2(double E0, double omega, double cycles, double t0, double h, long long ns,
                                          long long J, double *A, cudaStream_t stream);
 
+// Whole propagation of a small system in one CTA (small.cu): U in shared
+// memory, every RK4 stage / Taylor term of every step in one launch.
+struct SmallArgs {
+    const void *U;            // the context's dipole blocks (storage format of the precision)
+    long long bstride;
+    int ld, n, lmax;
+    long long N;
+    const double *E;
+    double2 *c;               // in/out
+    const double *field;
+    int sps, mode, order, hold, gauge;
+    long long nsteps;
+    double dt;
+};
+bool small_fits(int prec, int lmax, int n, int ld, long long N);
+cudaError_t launch_small(int prec, const SmallArgs &A, cudaStream_t stream);
+
 }  // namespace tdse
