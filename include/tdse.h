@@ -230,7 +230,7 @@ tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, 
  *   grad_field device, FP64, same length as field (overwritten).
  *   c_final    device, complex [N] or NULL: receives c(T).
  *   loss       device, FP64 [1] or NULL: receives L.
- * Errors: EINVAL, ENOMEM, ECUDA.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENOTSUP (TDSE_LANCZOS, BF16X3 contexts).
  */
 tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field,
                          int samples_per_step, double dt, long nsteps, tdse_scheme scheme,
