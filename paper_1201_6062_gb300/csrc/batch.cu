@@ -20,8 +20,8 @@ constexpr int BM = 128, BN = 128, BK = 16;
 __global__ void __launch_bounds__(256)
 bgemm_f32_kernel(BatchArgs A)
 {
-    __shared__ float As[BK][BM + 4];
-    __shared__ float Bs[BK][BN + 4];
+    __shared__ __align__(16) float As[BK][BM + 4];
+    __shared__ __align__(16) float Bs[BK][BN + 4];
     const int l = blockIdx.z;
     const int i0 = blockIdx.x * BM;
     const int c0 = blockIdx.y * BN;
@@ -30,11 +30,13 @@ bgemm_f32_kernel(BatchArgs A)
     const long long N = A.N;
     const int ncol = 2 * A.B;
     const float *U = reinterpret_cast<const float *>(A.U);
-    float acc[8][8];
+    // acc[r][p]: row r, columns (tx*4 + 2p, +1) for p < 2 and (64 + tx*4 + 2(p-2), +1) for p >= 2:
+    // the (Re, Im) planes of one pulse, updated together with paired FP32 instructions
+    float2 acc[8][4];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
+        for (int q = 0; q < 4; ++q) acc[r][q] = make_float2(0.f, 0.f);
 
     for (int part = 0; part < 2; ++part) {
         // part 0: U_l (rows of block l) times X_{l+1};  part 1: U_{l-1}^T times X_{l-1}
@@ -42,54 +44,67 @@ bgemm_f32_kernel(BatchArgs A)
         if (part == 1 && l < 1) continue;
         const float *Ub = U + (long long)(part == 0 ? l : l - 1) * A.bstride;
         const long long xbase = (long long)(part == 0 ? l + 1 : l - 1) * n;
-        for (int k0 = 0; k0 < n; k0 += BK) {
+        const float sgn = (part == 1 && A.gauge) ? -1.f : 1.f;     // velocity gauge: lower blocks -U^T
+        float ra[8], rb[8];
+        // tile k0 into registers: A[m][k] (part 0: U_l[i0+m][k0+k]; part 1: U_{l-1}[k0+k][i0+m]) and B[k][c]
+        auto load = [&](int k0) {
             if (part == 0) {
-                // A[m][k] = U_l[i0+m][k0+k]: thread -> row m = tid/2, 8 consecutive k
-                const int m = tid >> 1, kb = (tid & 1) * 8;
-                const int i = i0 + m;
+                const int m = tid >> 1, kb = (tid & 1) * 8, i = i0 + m;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int kk = k0 + kb + q;
-                    As[kb + q][m] = (i < n && kk < n) ? Ub[(long long)i * A.ld + kk] : 0.f;
+                    ra[q] = (i < n && kk < n) ? Ub[(long long)i * A.ld + kk] : 0.f;
                 }
             } else {
-                // A[m][k] = U_{l-1}[k0+k][i0+m]: thread -> k = tid/16, 8 consecutive m
-                const int kq = tid >> 4, mb = (tid & 15) * 8;
-                const int kk = k0 + kq;
+                const int kq = tid >> 4, mb = (tid & 15) * 8, kk = k0 + kq;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int i = i0 + mb + q;
-                    const float u = (i < n && kk < n) ? Ub[(long long)kk * A.ld + i] : 0.f;
-                    As[kq][mb + q] = A.gauge ? -u : u;
+                    ra[q] = (i < n && kk < n) ? sgn * Ub[(long long)kk * A.ld + i] : 0.f;
                 }
+            }
+            const int cc = tid >> 1, kb = (tid & 1) * 8, col = c0 + cc;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int kk = k0 + kb + q;
+                rb[q] = (col < ncol && kk < n) ? A.xin[(long long)col * N + xbase + kk] : 0.f;
+            }
+        };
+        load(0);
+        for (int k0 = 0; k0 < n; k0 += BK) {
+            __syncthreads();
+            if (part == 0) {
+                const int m = tid >> 1, kb = (tid & 1) * 8;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) As[kb + q][m] = ra[q];
+            } else {
+                const int kq = tid >> 4, mb = (tid & 15) * 8;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) As[kq][mb + q] = ra[q];
             }
             {
-                // B[k][c] = xin[plane c0+c][xbase + k0 + k]
                 const int cc = tid >> 1, kb = (tid & 1) * 8;
-                const int col = c0 + cc;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int kk = k0 + kb + q;
-                    Bs[kb + q][cc] = (col < ncol && kk < n) ? A.xin[(long long)col * N + xbase + kk] : 0.f;
-                }
+                for (int q = 0; q < 8; ++q) Bs[kb + q][cc] = rb[q];
             }
             __syncthreads();
+            if (k0 + BK < n) load(k0 + BK);                 // next tile's loads in flight during the products
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
-                float a[8], b[8];
+                const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + ty * 4]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][64 + tx * 4]);
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                                     make_float2(b1.z, b1.w)};
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    a[r] = As[kk][ty * 4 + r];
-                    a[4 + r] = As[kk][64 + ty * 4 + r];
-                    b[r] = Bs[kk][tx * 4 + r];
-                    b[4 + r] = Bs[kk][64 + tx * 4 + r];
+                for (int r = 0; r < 8; ++r) {
+                    const float2 ar = make_float2(a[r], a[r]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[r][q] = __ffma2_rn(ar, b[q], acc[r][q]);
                 }
-#pragma unroll
-                for (int r = 0; r < 8; ++r)
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(a[r], b[q], acc[r][q]);
             }
-            __syncthreads();
         }
     }
 
@@ -105,8 +120,7 @@ bgemm_f32_kernel(BatchArgs A)
             const int col = c0 + (p < 2 ? tx * 4 + 2 * p : 64 + tx * 4 + 2 * (p - 2));
             const int b = col >> 1;
             if (b >= A.B) continue;
-            const double dr = (double)acc[r][2 * p], di = (double)acc[r][2 * p + 1];
-            batch_update(A, b, a, e, dr, di);
+            batch_update(A, b, a, e, (double)acc[r][p].x, (double)acc[r][p].y);
         }
     }
 }
