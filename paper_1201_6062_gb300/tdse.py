@@ -308,10 +308,11 @@ _lib.tdse_group_tune.restype = _i
 
 
 class Group:
-    """Several Hamiltonians of different (lmax, n) advanced together: one
-    launch per stage for all of them (uneven batch).  The member Hamiltonians
-    must outlive the group and must not be propagated on their own while the
-    group runs (their scratch vectors are shared)."""
+    """Several Hamiltonians of different (lmax, n) advanced together (uneven
+    batch): per stage one product launch per thread-layout bucket and one
+    update launch for all, one RK4 step replayed as a CUDA graph.  The member
+    Hamiltonians must outlive the group and must not be propagated on their
+    own while the group runs (their scratch vectors are shared)."""
 
     def __init__(self, hams):
         self.hams = list(hams)
@@ -347,7 +348,8 @@ class Group:
         _check(_lib.tdse_group_sync(self._g, _stream(stream)))
 
     def tune(self, reps=3, stream=None):
-        """Autotune the ring-stage depth; returns (rows per stage, ms per product)."""
+        """Autotune the ring-stage depth of every bucket; returns (rows per
+        stage of the bucket with the most bytes, summed ms of one product)."""
         rs, ms = _i(), _d()
         _check(_lib.tdse_group_tune(self._g, int(reps), ctypes.byref(rs), ctypes.byref(ms), _stream(stream)))
         return rs.value, ms.value
