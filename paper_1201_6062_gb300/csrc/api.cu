@@ -620,9 +620,13 @@ static tdse_status propagate_impl(tdse_ctx *ctx, double *c, const double *field,
         A.gauge = ctx->desc.gauge;
         A.nsteps = nsteps;
         A.dt = dt;
-        CUDA_TRY(tdse::launch_small(ctx->prec, A, s));
-        ctx->launches += 1;
-        return TDSE_OK;
+        const cudaError_t e = tdse::launch_small(ctx->prec, A, s);
+        if (e == cudaSuccess) {
+            ctx->launches += 1;
+            return TDSE_OK;
+        }
+        // a cluster this size could not be placed: take the per-stage launches below
+        (void)cudaGetLastError();
     }
     CUDA_TRY(tdse::launch_prep(ctx->prec, ctx->plan.nblk, ctx->plan.blk.as<int2>(), ctx->sys.as<SysDesc>(), 0, s));
     ctx->launches += 1;
