@@ -85,6 +85,20 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
 {
     uint32_t r[32];
@@ -215,8 +229,8 @@ __device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, d
 // Two accumulators of TBN columns live in tensor memory, so the epilogue of
 // one tile runs while the products of the next are issued.
 constexpr int EPI_WARPS = 16;                       // a multiple of 4: EPI_WARPS / 4 per TMEM lane quarter
-constexpr int EPI_CPW = (TBN / 32) / (EPI_WARPS / 4); // 32-column accumulator chunks per epilogue warp
-static_assert(EPI_CPW * (EPI_WARPS / 4) * 32 == TBN, "epilogue warps must split the tile's columns evenly");
+constexpr int EPI_CPW = (TBN / 16) / (EPI_WARPS / 4); // 16-column accumulator chunks per epilogue warp
+static_assert(EPI_CPW * (EPI_WARPS / 4) * 16 == TBN, "epilogue warps must split the tile's columns evenly");
 constexpr int TC_LOAD_GROUP = 2;                   // pulses whose state loads are issued together
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA issuer, epilogue
 
@@ -350,23 +364,23 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
             if (valid_row) { const float2 ev = A.Edf[a]; e = df{ev.x, ev.y}; }
 #pragma unroll 1
             for (int chunk = part * EPI_CPW; chunk < (part + 1) * EPI_CPW; ++chunk) {
-                float v[32];
+                float v[16];
                 if (T > 0) {
-                    tmem_ld32(tmem + (uint32_t)(ab * TBN) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(chunk * 32), v);
+                    tmem_ld16(tmem + (uint32_t)(ab * TBN) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(chunk * 16), v);
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = 0.f;
+                    for (int q = 0; q < 16; ++q) v[q] = 0.f;
                 }
                 if (valid_row) {
                     const bool rk4 = A.mode == 2;
                     const bool from_c = rk4 ? (A.stage == 0) : (A.stage == 1);
 #pragma unroll
-                    for (int g = 0; g < 16; g += TC_LOAD_GROUP) {
+                    for (int g = 0; g < 8; g += TC_LOAD_GROUP) {
                         TcIn in[TC_LOAD_GROUP];
                         float2 fv[TC_LOAD_GROUP];
 #pragma unroll
                         for (int u = 0; u < TC_LOAD_GROUP; ++u) {
-                            const int b = c0 / 2 + chunk * 16 + g + u;     // pulse
+                            const int b = c0 / 2 + chunk * 8 + g + u;      // pulse
                             if (b < A.B) {
                                 tc_load(A, (long long)b * A.N + a, rk4, from_c, in[u]);
                                 fv[u] = __ldg(A.fdf + b);
@@ -375,7 +389,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
 #pragma unroll
                         for (int u = 0; u < TC_LOAD_GROUP; ++u) {
                             const int jj = g + u;
-                            const int b = c0 / 2 + chunk * 16 + jj;
+                            const int b = c0 / 2 + chunk * 8 + jj;
                             if (b < A.B) tc_update(A, b, a, e, df{fv[u].x, fv[u].y}, v[2 * jj], v[2 * jj + 1], in[u]);
                         }
                     }
