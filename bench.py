@@ -174,11 +174,19 @@ def whole_job_rate(world_size, units_per_rank, ms):
     return world_size * units_per_rank / (ms / 1e3)
 
 
-def cpu_baseline(cfg, seconds, E=None, U=None):
-    """The oracle as it stands on the host cores: RK4 steps of the same system
-    until `seconds` have elapsed (at least one step)."""
+def cpu_baseline(cfg, seconds, E=None, U=None, threads=None):
+    """The oracle as it stands on the host cores (all of them, or `threads`):
+    RK4 steps of the same system until `seconds` have elapsed (at least one
+    step)."""
     import oracle
     from paper_1201_6062_gb300 import inputs
+    if threads is not None:
+        prev = oracle.threads()
+        oracle.set_threads(threads)
+        try:
+            return cpu_baseline(cfg, seconds, E, U)
+        finally:
+            oracle.set_threads(prev)
     lmax, n, dt = cfg["lmax"], cfg["n"], cfg["dt"]
     if E is None:
         E = inputs.energies(lmax, n)
@@ -195,7 +203,7 @@ def cpu_baseline(cfg, seconds, E=None, U=None):
             break
     N = (lmax + 1) * n
     return {"value": N * steps / el, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": "%d RK4 steps of the lmax=31 n=2000 system (%.1f s)" % (steps, el)}
+            "sample": "%d RK4 steps of the lmax=%d n=%d system (%.1f s)" % (steps, lmax, n, el)}
 
 
 def run_reference(args):
@@ -619,9 +627,11 @@ def run_ours(args):
     if rank == 0 and not args.no_adjoint:
         adjoint = adjoint_section(args)
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg, args.cpu_seconds, E, U)
+        # one core, as the paper's serial-CPU comparison (context only)
+        cpu1 = cpu_baseline(cfg, args.cpu_seconds / 2, E, U, threads=1)
 
     if rank == 0:
         line = {
@@ -630,7 +640,7 @@ def run_ours(args):
             "dtype": {"df32": "f32x2 (float-float products, FP64 state)", "fp64": "f64",
                       "fp32": "f32 products, FP64 state"}[primary],
             "data": "synthetic", "config": config_dict(cfg, primary),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_single_core": cpu1, "e2e": e2e, "clocks": clocks,
             "gpu_launches": p["gpu_launches"],
             "variants": res,
             "pulse_sweep": sweep,
