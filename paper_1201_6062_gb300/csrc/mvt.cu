@@ -276,7 +276,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
 // ------------------------------------------------------ instantiations --
 // (CT, MAXG) thread layouts; RS in {1, 2, 4, 8} rows per stage.
 struct TCfg { int CT, MAXG; };
-static const TCfg kTCfg[] = {{128, 1}, {128, 2}, {256, 2}, {256, 3}, {256, 4}, {512, 4}};
+static const TCfg kTCfg[] = {{128, 1}, {128, 2}, {192, 2}, {256, 2}, {192, 3}, {256, 3}, {256, 4}, {512, 4}};
 constexpr int kNumTCfg = sizeof(kTCfg) / sizeof(kTCfg[0]);
 
 template <class P, int CT, int MAXG>
@@ -297,10 +297,12 @@ static const void *mvt_fn(int idx, int rs)
     switch (idx) {
     case 0: return mvt_fn_rs<P, 128, 1>(rs);
     case 1: return mvt_fn_rs<P, 128, 2>(rs);
-    case 2: return mvt_fn_rs<P, 256, 2>(rs);
-    case 3: return mvt_fn_rs<P, 256, 3>(rs);
-    case 4: return mvt_fn_rs<P, 256, 4>(rs);
-    case 5: return rs <= 2 ? mvt_fn_rs<P, 512, 4>(rs) : nullptr;
+    case 2: return mvt_fn_rs<P, 192, 2>(rs);
+    case 3: return mvt_fn_rs<P, 256, 2>(rs);
+    case 4: return mvt_fn_rs<P, 192, 3>(rs);
+    case 5: return mvt_fn_rs<P, 256, 3>(rs);
+    case 6: return mvt_fn_rs<P, 256, 4>(rs);
+    case 7: return rs <= 2 ? mvt_fn_rs<P, 512, 4>(rs) : nullptr;
     }
     return nullptr;
 }
