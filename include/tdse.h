@@ -11,7 +11,15 @@
  * amplitudes [l*n, (l+1)*n)).  By the dipole selection rule (Sec. 3.1,
  * Fig. "Matrix") D couples only neighbouring blocks: D_{l,l+1} = U_l is a
  * dense real n x n block and D_{l+1,l} = U_l^T (Sec. 5: only the upper blocks
- * are stored).  f(t) is the electric-field sample (length gauge, Sec. 5).
+ * are stored).  f(t) is the electric-field sample (length gauge, Sec. 5);
+ * tdse_set_gauge selects the velocity gauge instead (f(t) = A(t), D = i K).
+ *
+ * Entry points: contexts (tdse_create / tdse_destroy), one product
+ * (tdse_hmatvec), propagation (tdse_propagate: RK4, Taylor, Lanczos;
+ * tdse_propagate_host; tdse_propagate_rkf45: adaptive), pulse batches
+ * (tdse_propagate_batch), uneven batches (tdse_group_*), the adjoint
+ * (tdse_adjoint), norms and populations, the velocity-gauge field
+ * (tdse_vector_potential_sin2), tracing (tdse_profile_*).
  *
  * Common conventions
  *  - Complex vectors are interleaved (re, im) FP64 pairs, i.e. the memory of
