@@ -143,7 +143,12 @@ static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std:
     mp.max_ld = ldmax;
     int G;
     if (tdse::mvt_config(prec, nmax, ldmax, &mp.cfg)) {
-        G = sm_count();                         // one ring CTA per SM (shared memory bound)
+        // Several ring CTAs per SM when short rows leave shared memory for them,
+        // but only for dipole blocks streamed from HBM: when they stay in L2,
+        // more CTAs only add column-partial slots and per-CTA overhead.
+        long long ubytes = 0;
+        for (size_t q = 0; q < n.size(); ++q) ubytes += (long long)lmax[q] * n[q] * n[q] * elem_bytes(prec);
+        G = sm_count() * (ubytes >= (64LL << 20) ? tdse::mvt_ctas_per_sm(prec, mp.cfg) : 1);
     } else {
         if (!tdse::mv_config(prec, nmax, &mp.cfg)) return fail(TDSE_ENOTSUP, "n=%d exceeds the supported maximum", nmax);
         G = sm_count() * tdse::mv_ctas_per_sm(prec, mp.cfg);

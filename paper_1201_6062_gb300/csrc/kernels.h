@@ -15,6 +15,7 @@ struct MvCfg {
     int CT, RW, MAXG, BT;
     int tma = 0;        // 1: bulk-copy ring kernel (mvt.cu), 0: per-thread loads (mv.cu)
     int RS = 0;         // rows per ring stage (tma only)
+    int ld = 0;         // largest row stride the configuration serves (tma only): stage = RS rows of it
 };
 
 // Launch with programmatic stream serialization (the kernel calls pdl_wait()
@@ -28,6 +29,9 @@ int mv_ctas_per_sm(int prec, const MvCfg &cfg);
 // Ring-fed variant for rows of more than 32 column groups; false if n/ld do
 // not qualify.
 bool mvt_config(int prec, int n, int ld, MvCfg *out);
+// Resident ring CTAs per SM for a configuration (its ring is NS stages of RS
+// rows of the longest stride, so short rows fit several CTAs per SM).
+int mvt_ctas_per_sm(int prec, const MvCfg &cfg);
 // Sets the kernel attributes a launch needs (call outside stream capture).
 cudaError_t mvt_prepare(int prec, const MvCfg &cfg);
 // Whether `rs` rows per stage fit the ring for rows of `ld` elements.

@@ -20,13 +20,14 @@ namespace tdse {
 constexpr int RBT = 16;                // rows per row-sum reduction chunk (and column-sum fold)
 constexpr int RS_MAX = 8;              // rows per ring stage: 1, 2, 4 or 8
 constexpr int NS = 3;                  // ring stages
-constexpr int STAGE_MAX = 65536;       // bytes of dipole rows per stage
+constexpr int STAGE_MAX = 65536;       // bytes of dipole rows per stage, at most (the launch sizes
+                                       // each stage to RS rows of the longest row stride it serves)
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
 
 template <class P, int CT, int MAXG, int RS>
 __global__ void __launch_bounds__(CT + 32, 1)
 mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const int *__restrict__ cta_off,
-           int *__restrict__ err)
+           int *__restrict__ err, int stage)
 {
     constexpr int CW = P::CW;
     constexpr int NW = CT / 32;
@@ -92,7 +93,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     const uint32_t bytes = (uint32_t)(nr * ld * (long long)sizeof(Elem));
                     const uint32_t xbytes = (uint32_t)(nr * 16);
                     mbar_arrive_expect_tx(&full[s], bytes + xbytes);
-                    bulk_g2s(ring + (size_t)s * STAGE_MAX, Ub + (long long)r * ld, bytes, &full[s], pol);
+                    bulk_g2s(ring + (size_t)s * stage, Ub + (long long)r * ld, bytes, &full[s], pol);
                     bulk_g2s(&xs_raw[s][0], reinterpret_cast<const char *>(S.xq) + (base_l + r) * 16, xbytes, &full[s],
                              pol_x);
                 }
@@ -164,7 +165,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     for (int rr = 0; rr < RS; ++rr) { rre[rr] = P::rzero(sig); rim[rr] = P::rzero(sig); }
                     const bool live = mbar_wait_bounded(&full[s], (uint32_t)((q / NS) & 1), abort, WAIT_NS);
                     if (live) {
-                        const Elem *st_rows = reinterpret_cast<const Elem *>(ring + (size_t)s * STAGE_MAX);
+                        const Elem *st_rows = reinterpret_cast<const Elem *>(ring + (size_t)s * stage);
                         typename P::Uv u[RS][MAXG][CW];
                         XV xi[RS];
 #pragma unroll
@@ -334,6 +335,7 @@ bool mvt_config(int prec, int n, int ld, MvCfg *out)
             *out = MvCfg{i, kTCfg[i].CT, 1, kTCfg[i].MAXG, kTCfg[i].CT + 32};
             out->tma = 1;
             out->RS = rs;
+            out->ld = ld;
             return true;
         }
     }
@@ -354,20 +356,41 @@ cudaError_t mvt_prepare(int prec, const MvCfg &cfg)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, NS * STAGE_MAX);
 }
 
+// Bytes per ring stage: RS rows of the longest stride, rounded to 128.
+static int stage_bytes(int prec, const MvCfg &cfg)
+{
+    const long long b = (long long)cfg.RS * cfg.ld * elem_size(prec);
+    return (int)((b + 127) & ~127LL);
+}
+
+int mvt_ctas_per_sm(int prec, const MvCfg &cfg)
+{
+    const void *fn = mvt_fn_prec(prec, cfg.idx, cfg.RS);
+    if (!fn || cfg.ld <= 0) return 1;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, NS * STAGE_MAX) != cudaSuccess) return 1;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, cfg.BT, (size_t)NS * stage_bytes(prec, cfg)) !=
+        cudaSuccess)
+        return 1;
+    return nb < 1 ? 1 : nb;
+}
+
 cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys, const Seg *segs,
                        const int *cta_off, int *err, cudaStream_t stream)
 {
     const void *fn = mvt_fn_prec(prec, cfg.idx, cfg.RS);
-    if (!fn) return cudaErrorInvalidValue;
+    if (!fn || cfg.ld <= 0) return cudaErrorInvalidValue;
     if (grid <= 0) return cudaSuccess;
-    const int smem = NS * STAGE_MAX;
+    int stage = stage_bytes(prec, cfg);
+    if (stage > STAGE_MAX) return cudaErrorInvalidValue;
+    const int smem = NS * stage;
     static bool attr_done[3][kNumTCfg][9] = {};
     if (!attr_done[prec][cfg.idx][cfg.RS]) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, NS * STAGE_MAX);
         if (e != cudaSuccess) return e;
         attr_done[prec][cfg.idx][cfg.RS] = true;
     }
-    void *args[] = {(void *)&sys, (void *)&segs, (void *)&cta_off, (void *)&err};
+    void *args[] = {(void *)&sys, (void *)&segs, (void *)&cta_off, (void *)&err, (void *)&stage};
     return launch_pdl(fn, dim3(grid), dim3(cfg.BT), (size_t)smem, stream, args);
 }
 
