@@ -18,6 +18,10 @@ struct MvCfg {
     int ld = 0;         // largest row stride the configuration serves (tma only): stage = RS rows of it
 };
 
+// Raise fn's dynamic shared memory limit to `bytes` on the current device
+// (once per device and kernel; thread-safe).
+cudaError_t ensure_dyn_smem(const void *fn, int bytes);
+
 // Launch with programmatic stream serialization (the kernel calls pdl_wait()
 // before reading what earlier kernels wrote).
 cudaError_t launch_pdl(const void *fn, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, void **args);

@@ -15,6 +15,10 @@
 // epilogue adds the slots of a block in slot order, so every result is
 // bitwise reproducible (no atomics).  FP64 state; dipole products in the
 // arithmetic of the precision policy (common.cuh).
+#include <mutex>
+#include <set>
+#include <tuple>
+
 #include "kernels.h"
 #include "epi.cuh"
 #include "sync.cuh"
@@ -284,6 +288,21 @@ prep_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, int f
     const long long a = (long long)bm.y + threadIdx.x;
     if (a >= S.N) return;
     P::store_xq(S.xq, a, from_x ? S.x[a] : S.c[a]);
+}
+
+cudaError_t ensure_dyn_smem(const void *fn, int bytes)
+{
+    static std::mutex mu;
+    static std::set<std::tuple<int, const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(dev, fn, bytes);
+    if (done.count(key)) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
 }
 
 cudaError_t launch_pdl(const void *fn, dim3 grid, dim3 block, size_t smem, cudaStream_t stream, void **args)

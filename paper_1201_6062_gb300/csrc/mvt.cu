@@ -353,7 +353,7 @@ cudaError_t mvt_prepare(int prec, const MvCfg &cfg)
 {
     const void *fn = mvt_fn_prec(prec, cfg.idx, cfg.RS);
     if (!fn) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, NS * STAGE_MAX);
+    return ensure_dyn_smem(fn, NS * STAGE_MAX);
 }
 
 // Bytes per ring stage: RS rows of the longest stride, rounded to 128.
@@ -367,7 +367,7 @@ int mvt_ctas_per_sm(int prec, const MvCfg &cfg)
 {
     const void *fn = mvt_fn_prec(prec, cfg.idx, cfg.RS);
     if (!fn || cfg.ld <= 0) return 1;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, NS * STAGE_MAX) != cudaSuccess) return 1;
+    if (ensure_dyn_smem(fn, NS * STAGE_MAX) != cudaSuccess) return 1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, cfg.BT, (size_t)NS * stage_bytes(prec, cfg)) !=
         cudaSuccess)
@@ -384,12 +384,8 @@ cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys,
     int stage = stage_bytes(prec, cfg);
     if (stage > STAGE_MAX) return cudaErrorInvalidValue;
     const int smem = NS * stage;
-    static bool attr_done[3][kNumTCfg][9] = {};
-    if (!attr_done[prec][cfg.idx][cfg.RS]) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, NS * STAGE_MAX);
-        if (e != cudaSuccess) return e;
-        attr_done[prec][cfg.idx][cfg.RS] = true;
-    }
+    const cudaError_t e = ensure_dyn_smem(fn, NS * STAGE_MAX);
+    if (e != cudaSuccess) return e;
     void *args[] = {(void *)&sys, (void *)&segs, (void *)&cta_off, (void *)&err, (void *)&stage};
     return launch_pdl(fn, dim3(grid), dim3(cfg.BT), (size_t)smem, stream, args);
 }

@@ -180,12 +180,8 @@ cudaError_t launch_small(int prec, const SmallArgs &A, cudaStream_t stream)
     case 2: fn = (const void *)small_kernel<PolDF32>; break;
     default: return cudaErrorInvalidValue;
     }
-    static bool attr[3] = {false, false, false};
-    if (!attr[prec]) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
-        if (e != cudaSuccess) return e;
-        attr[prec] = true;
-    }
+    const cudaError_t e = ensure_dyn_smem(fn, (int)SMEM_MAX);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(SCL);
     cfg.blockDim = dim3(SNT);

@@ -17,6 +17,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "kernels.h"
 #include "sync.cuh"
 #include "tc.h"
 
@@ -450,14 +451,10 @@ __global__ void tc_out_kernel(const float4 *__restrict__ cdf, double2 *__restric
 
 cudaError_t launch_tc(const TcMaps &m, const TcArgs &A, cudaStream_t stream)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    static int sms = 0;
-    if (!sms) {
+    const cudaError_t ea = ensure_dyn_smem((const void *)tc_kernel, TC_SMEM);
+    if (ea != cudaSuccess) return ea;
+    int sms = 0;
+    {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
