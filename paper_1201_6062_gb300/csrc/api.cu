@@ -148,7 +148,8 @@ static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std:
         // more CTAs only add column-partial slots and per-CTA overhead.
         long long ubytes = 0;
         for (size_t q = 0; q < n.size(); ++q) ubytes += (long long)lmax[q] * n[q] * n[q] * elem_bytes(prec);
-        G = sm_count() * (ubytes >= (64LL << 20) ? tdse::mvt_ctas_per_sm(prec, mp.cfg) : 1);
+        mp.cfg.per_sm = ubytes >= (64LL << 20) ? tdse::mvt_ctas_per_sm(prec, mp.cfg) : 1;
+        G = sm_count() * mp.cfg.per_sm;
     } else {
         if (!tdse::mv_config(prec, nmax, &mp.cfg)) return fail(TDSE_ENOTSUP, "n=%d exceeds the supported maximum", nmax);
         G = sm_count() * tdse::mv_ctas_per_sm(prec, mp.cfg);

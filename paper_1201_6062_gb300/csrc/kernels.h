@@ -16,6 +16,7 @@ struct MvCfg {
     int tma = 0;        // 1: bulk-copy ring kernel (mvt.cu), 0: per-thread loads (mv.cu)
     int RS = 0;         // rows per ring stage (tma only)
     int ld = 0;         // largest row stride the configuration serves (tma only): stage = RS rows of it
+    int per_sm = 1;     // ring CTAs the plan places on each SM (tma only); 1: each CTA holds an SM alone
 };
 
 // Raise fn's dynamic shared memory limit to `bytes` on the current device

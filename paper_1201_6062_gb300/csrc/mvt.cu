@@ -383,7 +383,9 @@ cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys,
     if (grid <= 0) return cudaSuccess;
     int stage = stage_bytes(prec, cfg);
     if (stage > STAGE_MAX) return cudaErrorInvalidValue;
-    const int smem = NS * stage;
+    // A plan of one CTA per SM requests the whole ring so that no two of its
+    // CTAs share an SM (the work split assumes every CTA has one to itself).
+    const int smem = cfg.per_sm > 1 ? NS * stage : NS * STAGE_MAX;
     const cudaError_t e = ensure_dyn_smem(fn, NS * STAGE_MAX);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&sys, (void *)&segs, (void *)&cta_off, (void *)&err, (void *)&stage};
