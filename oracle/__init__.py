@@ -15,9 +15,12 @@ Functions follow the paper (Ó Broin & Nikolopoulos, arXiv:1201.6062):
   adjoint             discrete adjoint of rk4 / taylor (the paper has no adjoint;
                       pinned by finite differences and a forward-mode tangent)
 """
+import contextlib
 import ctypes
 import os
+import shutil
 import subprocess
+import tempfile
 
 import numpy as np
 
@@ -38,36 +41,70 @@ def build(force=False):
     return _LIB
 
 
+def _open(path):
+    lib = ctypes.CDLL(path)
+    _declare(lib)
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        L, I, D = ctypes.c_long, ctypes.c_int, ctypes.c_double
-        lib.orc_threads.restype = I
-        lib.orc_set_threads.argtypes = [I]
-        lib.orc_dmatvec.argtypes = [I, I, _dp, _dp, _dp]
-        lib.orc_hmatvec.argtypes = [I, I, _dp, _dp, D, _dp, _dp]
-        lib.orc_field_at.argtypes = [_dp, I, L, I]
-        lib.orc_field_at.restype = D
-        lib.orc_rk4.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L]
-        lib.orc_rk4.restype = L
-        lib.orc_taylor.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I]
-        lib.orc_taylor.restype = L
-        lib.orc_lanczos.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I]
-        lib.orc_lanczos.restype = L
-        lib.orc_tridiag_eig.argtypes = [I, _dp, _dp, _dp]
-        lib.orc_tridiag_eig.restype = I
-        lib.orc_populations.argtypes = [I, I, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
-        lib.orc_set_gauge.argtypes = [I]
-        lib.orc_vector_potential_sin2.argtypes = [D, D, D, D, D, L, _dp]
-        lib.orc_rkf45_tableau.argtypes = [_dp, _dp, _dp, _dp]
-        lib.orc_rkf45.argtypes = [I, I, _dp, _dp, _dp, I, D, D, D, D, D, D, D, D, D, D, L,
-                                  ctypes.POINTER(L), _dp]
-        lib.orc_rkf45.restype = L
-        lib.orc_adjoint.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I, I, _dp, _dp, _dp]
-        _lib = lib
+        _lib = _open(_LIB)
     return _lib
+
+
+@contextlib.contextmanager
+def variant(source_text, tag):
+    """Mutation testing: compile `source_text` (a modified tdse_oracle.c) in a
+    temporary directory and route every wrapper of this module through it
+    inside the `with` block."""
+    global _lib
+    d = tempfile.mkdtemp(prefix="oracle_%s_" % tag)
+    src, so = os.path.join(d, "v.c"), os.path.join(d, "libv.so")
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", so, src, "-lm"])
+    saved = _lib
+    _lib = _open(so)
+    try:
+        yield
+    finally:
+        _lib = saved
+        shutil.rmtree(d, ignore_errors=True)
+
+
+def source():
+    """The oracle's C source text (for mutation tests)."""
+    with open(_SRC) as f:
+        return f.read()
+
+
+def _declare(lib):
+    L, I, D = ctypes.c_long, ctypes.c_int, ctypes.c_double
+    lib.orc_threads.restype = I
+    lib.orc_set_threads.argtypes = [I]
+    lib.orc_dmatvec.argtypes = [I, I, _dp, _dp, _dp]
+    lib.orc_hmatvec.argtypes = [I, I, _dp, _dp, D, _dp, _dp]
+    lib.orc_field_at.argtypes = [_dp, I, L, I]
+    lib.orc_field_at.restype = D
+    lib.orc_rk4.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L]
+    lib.orc_rk4.restype = L
+    lib.orc_taylor.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I]
+    lib.orc_taylor.restype = L
+    lib.orc_lanczos.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I]
+    lib.orc_lanczos.restype = L
+    lib.orc_tridiag_eig.argtypes = [I, _dp, _dp, _dp]
+    lib.orc_tridiag_eig.restype = I
+    lib.orc_populations.argtypes = [I, I, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.orc_set_gauge.argtypes = [I]
+    lib.orc_vector_potential_sin2.argtypes = [D, D, D, D, D, L, _dp]
+    lib.orc_rkf45_tableau.argtypes = [_dp, _dp, _dp, _dp]
+    lib.orc_rkf45.argtypes = [I, I, _dp, _dp, _dp, I, D, D, D, D, D, D, D, D, D, D, L,
+                              ctypes.POINTER(L), _dp]
+    lib.orc_rkf45.restype = L
+    lib.orc_adjoint.argtypes = [I, I, _dp, _dp, _dp, _dp, I, D, L, I, I, I, _dp, _dp, _dp]
 
 
 def _p(a):

@@ -1,0 +1,49 @@
+"""Planted mistakes: each test compiles the oracle with one plausible error
+(a transposed block, a wrong weight or coefficient, a dropped term, a wrong
+sign) and checks that the pins of test_oracle_pins.py catch it.  The
+mutations live only in temporary copies of the oracle's C source."""
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+MUTANTS = [
+    ("lower_block_not_transposed",
+     "colsum[2 * j] += row[j] * xr;", "colsum[2 * j] += Ul[(long)j * n + i] * xr;",
+     lambda: pins.test_dmatvec_matches_dense_bruteforce(2, 4)),
+    ("rk4_weight",
+     "k1[q] + 2.0 * k2[q] + 2.0 * k3[q] + k4[q]", "k1[q] + 1.0 * k2[q] + 2.0 * k3[q] + k4[q]",
+     lambda: pins.test_field_free_rk4_is_stability_polynomial(1)),
+    ("taylor_term_factor",
+     "T[q] = (dt / m) * Tn[q];", "T[q] = (dt / (m + 1)) * Tn[q];",
+     lambda: pins.test_field_free_taylor_is_truncated_exponential(6)),
+    ("half_step_field",
+     "return 0.5 * (F[k] + F[k + 1]);", "return F[k];",
+     lambda: pins.test_step_grid_samples_interpolate_linearly()),
+    ("velocity_gauge_sign",
+     "const double re = up[2 * a] - dn[2 * a], im = up[2 * a + 1] - dn[2 * a + 1];",
+     "const double re = up[2 * a] + dn[2 * a], im = up[2 * a + 1] + dn[2 * a + 1];",
+     lambda: pins.test_velocity_gauge_product_matches_dense_bruteforce(2, 3)),
+    ("fehlberg_coefficient",
+     "-845.0 / 4104.0, 0.0},", "-845.0 / 4105.0, 0.0},",
+     lambda: pins.test_rkf45_tableau_satisfies_the_order_conditions()),
+    ("gauss_legendre_weight",
+     "const double w1 = (322.0 + 13.0 * sqrt(70.0)) / 900.0", "const double w1 = (322.0 + 13.0 * sqrt(70.0)) / 901.0",
+     lambda: pins.test_vector_potential_gauss_legendre_matches_the_closed_form()),
+    ("adjoint_loss_gradient",
+     "G[2 * a] = 2.0 * w[a] * cT[2 * a];", "G[2 * a] = w[a] * cT[2 * a];",
+     lambda: pins.test_adjoint_matches_central_differences("rk4", 4, 1, 0)),
+    ("lanczos_three_term_recurrence",
+     "if (j > 0) w[q] -= be[j] * V[(long)(j - 1) * 2 * N + q];", "(void)0;",
+     lambda: pins.test_lanczos_full_krylov_space_is_the_exact_exponential()),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_a_planted_mistake(name, old, new, pin):
+    src = oracle.source()
+    assert src.count(old) == 1, "mutation site not found: " + name
+    with oracle.variant(src.replace(old, new), name):
+        with pytest.raises(AssertionError):
+            pin()
+    pin()                       # the unmutated oracle passes the same pin
