@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--sweep-pulses", type=int, default=256)
     p.add_argument("--no-uneven", action="store_true", help="skip the uneven-batch (64 systems) section")
     p.add_argument("--no-small", action="store_true", help="skip the small-system section")
+    p.add_argument("--no-schemes", action="store_true", help="skip the Taylor / Lanczos / RKF45 / gauge section")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient section")
     p.add_argument("--accuracy-steps", type=int, default=2000,
                    help="steps of the error pass (the workload's 2000-step window; 0 skips it)")
@@ -361,6 +362,78 @@ def small_section(args):
     return out
 
 
+def schemes_section(args):
+    """The propagators of the large system (FP32 products) over one window of
+    1 a.u. starting at t = 20 a.u. (field on): RK4 (dt 0.01), Taylor-8 with H
+    frozen at mid-step (dt 0.02), short-iterative Lanczos with m = 10 (dt 0.05),
+    adaptive RKF 4(5) (tol 1e-9, the analytic sin^2 field) and RK4 in the
+    velocity gauge (A(t) samples from tdse_vector_potential_sin2).  Reports
+    the time, the number of block products, the time per product (the
+    scheme's overhead over the bare product) and the difference of the final
+    state from the RK4 one (the velocity-gauge run is a different gauge and
+    reports its norm drift instead)."""
+    import torch
+    from paper_1201_6062_gb300 import inputs, tdse
+    cfg = workload()
+    lmax, n = cfg["lmax"], cfg["n"]
+    E0, om = cfg["E0"], cfg["omega"]
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, cfg["seed"])
+    H = tdse.Hamiltonian(E, U, lmax, n, "fp32")
+    c0 = inputs.ground_state(lmax, n)
+    t0, T = 20.0, 1.0
+    out = {"workload": "large system lmax=31 n=2000, FP32 products, window t=20..21 a.u."}
+
+    def timed(fn):
+        c = torch.from_numpy(c0.copy()).cuda()
+        H.profile(True)                                  # untimed run: count the block products launched
+        H.profile_read()
+        fn(c)
+        H.sync()
+        _, nmv, _ = H.profile_read()
+        H.profile(False)
+        c = torch.from_numpy(c0.copy()).cuda()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = fn(c)
+        e1.record()
+        e1.synchronize()
+        return c.cpu().numpy(), e0.elapsed_time(e1), nmv, info
+
+    runs = {
+        "rk4": (0.01, lambda c: H.propagate(c, torch.from_numpy(inputs.field_samples(E0, om, 0.01, 100, 1, t0=t0)).cuda(),
+                                              0.01, 100)),
+        "taylor8_mid": (0.02, lambda c: H.propagate(c, torch.from_numpy(inputs.field_samples(E0, om, 0.02, 50, 2, t0=t0)).cuda(),
+                                                      0.02, 50, scheme="taylor", order=8, hold=1, samples_per_step=2)),
+        "lanczos10_mid": (0.05, lambda c: H.propagate(c, torch.from_numpy(inputs.field_samples(E0, om, 0.05, 20, 2, t0=t0)).cuda(),
+                                                        0.05, 20, scheme="lanczos", order=10, hold=1, samples_per_step=2)),
+        "rkf45": (None, lambda c: H.propagate_rkf45(c, t0, t0 + T, 0.01, 1e-9, field="sin2", E0=E0, omega=om,
+                                                    cycles=10, dt_min=1e-5)),
+    }
+    ref = None
+    for name, (dt, fn) in runs.items():
+        got, ms, nmv, info = timed(fn)
+        if ref is None:
+            ref = got
+        d = {"ms": ms, "products": nmv, "ms_per_product": ms / max(nmv, 1),
+             "rel_diff_vs_rk4": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+        if dt:
+            d["dt"] = dt
+        if isinstance(info, dict):
+            d.update({k: info[k] for k in ("accepted", "rejected")})
+        out[name] = d
+    # velocity gauge: the same RK4 window with A(t) from the Gauss-Legendre kernel
+    H.set_gauge("velocity")
+    A = tdse.vector_potential_sin2(E0, om, 10, t0, 0.01, 101)
+    got, ms, nmv, _ = timed(lambda c: H.propagate(c, A, 0.01, 100))
+    out["rk4_velocity_gauge"] = {"ms": ms, "products": nmv, "ms_per_product": ms / max(nmv, 1),
+                                 "norm_drift": float(abs(np.vdot(got, got).real - 1.0))}
+    H.close()
+    return out
+
+
 def uneven_section(args):
     """64 systems of different (lmax, n) (lmax 4..32, n 200..1500, each its own
     pulse) advanced together by tdse_group_propagate: RK4 amplitude-updates/s
@@ -630,6 +703,10 @@ def run_ours(args):
     if rank == 0 and not args.no_small:
         small = small_section(args)
 
+    schemes = None
+    if rank == 0 and not args.no_schemes:
+        schemes = schemes_section(args)
+
     uneven = None
     if rank == 0 and not args.no_uneven:
         uneven = uneven_section(args)
@@ -656,6 +733,7 @@ def run_ours(args):
             "variants": res,
             "pulse_sweep": sweep,
             "small_system": small,
+            "schemes": schemes,
             "uneven_batch": uneven,
             "adjoint": adjoint,
         }
