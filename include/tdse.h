@@ -61,6 +61,9 @@ typedef enum {
                            `taylor_order` = Krylov dimension m (1..32) products per
                            step, H frozen at the time `taylor_hold` selects, then
                            c <- |c| V exp(-i T dt) e_1 with T the Lanczos tridiagonal.
+                           A step with |T - sigma| |dt| > 4096 (sigma the centre
+                           of T's Gershgorin interval) is not formed: the state
+                           becomes invalid and the next tdse_sync fails.
                            tdse_propagate / tdse_propagate_host only.              */
 } tdse_scheme;
 
@@ -175,7 +178,9 @@ tdse_status tdse_propagate_host(tdse_ctx *ctx, double *c_host, const double *fie
  * failures of this context's kernels since the last check: TDSE_ETIMEOUT if a
  * bounded wait inside a kernel gave up (every such wait stops after 2 s; the
  * kernel then finishes without further waiting, and the results of the calls
- * since the last check are invalid).  Clears the device status word.
+ * since the last check are invalid); TDSE_EINVAL if a TDSE_LANCZOS step was
+ * out of range (see tdse_scheme; that state is invalid).  Clears the device
+ * status word.
  * Errors: EINVAL, ECUDA, ETIMEOUT.
  */
 tdse_status tdse_sync(tdse_ctx *ctx, void *stream);

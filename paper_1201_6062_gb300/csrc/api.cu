@@ -19,6 +19,7 @@
 #include "plan.h"
 #include "tc.h"
 #include "lanczos.h"
+#include "sync.cuh"
 #include "rkf.h"
 
 using tdse::SysDesc;
@@ -579,18 +580,16 @@ static tdse_status propagate_lanczos(tdse_ctx *ctx, double *c, int sps, double d
         CUDA_TRY(tdse::lz_launch_init(ctx->prec, sys, N, (const double2 *)c, pa, V, scal, s));
         ctx->launches += 2;
         for (int j = 0; j < m; ++j) {
+            // the product of j > 0 is taken of the unnormalised w; lz_apply scales it
             double2 *vj = V + (size_t)j * N;
             tdse_status st = launch_product(ctx, 0, s);
             if (st != TDSE_OK) return st;
-            CUDA_TRY(tdse::lz_launch_apply(sys, N, vj, w, A, pa, s));
-            CUDA_TRY(tdse::lz_launch_orth(sys, N, vj, j > 0 ? vj - N : vj, w, j, pa, scal, pb, s));
+            CUDA_TRY(tdse::lz_launch_apply(sys, N, j, vj, w, A, pb, scal, pa, s));
+            CUDA_TRY(tdse::lz_launch_orth(ctx->prec, sys, N, vj, j > 0 ? vj - N : vj, w, j, j + 1 == m ? 1 : 0, pa,
+                                          scal, pb, s));
             ctx->launches += 2;
-            if (j + 1 < m) {
-                CUDA_TRY(tdse::lz_launch_next(ctx->prec, sys, N, w, vj + N, j, pb, scal, s));
-                ctx->launches += 1;
-            }
         }
-        CUDA_TRY(tdse::lz_launch_small(scal, m, dt, s));
+        CUDA_TRY(tdse::lz_launch_small(scal, m, dt, ctx->errw.as<int>(), s));
         CUDA_TRY(tdse::lz_launch_combine(sys, N, V, m, scal, (double2 *)c, s));
         ctx->launches += 2;
     }
@@ -840,8 +839,12 @@ tdse_status tdse_sync(tdse_ctx *ctx, void *stream)
     CUDA_TRY(cudaMemcpy(&w, ctx->errw.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (w) {
         CUDA_TRY(cudaMemset(ctx->errw.p, 0, sizeof(int)));
-        return fail(TDSE_ETIMEOUT, "a bounded device-side wait gave up (status word 0x%x); the results of the "
-                                   "calls since the last check are invalid", w);
+        if (w & tdse::kErrTimeout)
+            return fail(TDSE_ETIMEOUT, "a bounded device-side wait gave up (status word 0x%x); the results of the "
+                                       "calls since the last check are invalid", w);
+        return fail(TDSE_EINVAL, "a Lanczos step had |T dt| beyond %d or a non-finite Krylov matrix (status word "
+                                 "0x%x): dt is too long for this Hamiltonian, and the state is invalid",
+                    tdse::LZ_SUBSTEP_MAX, w);
     }
     return TDSE_OK;
 }

@@ -50,3 +50,39 @@ def test_lanczos_is_reproducible_and_rejects_large_krylov_spaces(tdse_lib):
     assert torch.equal(a, b)
     with pytest.raises(tdse_lib.TDSEError):
         H.propagate(a, F, 0.05, 10, "lanczos", order=33)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df32"])
+def test_lanczos_long_steps_take_substeps(tdse_lib, prec):
+    """dt = 0.8 puts |T dt| above 1, so the device exponential of the Krylov
+    matrix runs several Taylor substeps; the oracle diagonalises T instead."""
+    lmax, n, m = 2, 40, 10
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, 77)
+    dt, nsteps = 0.8, 6
+    F = inputs.field_samples(0.2, 0.6, dt, nsteps, 1, cycles=2, t0=1.0)
+    c0 = inputs.random_state((lmax + 1) * n, 78)
+    ref, _ = oracle.lanczos(lmax, n, E, U, c0, F, dt, nsteps, m, hold=0)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, prec)
+    c = torch.from_numpy(c0.copy()).cuda()
+    H.propagate(c, torch.from_numpy(F).cuda(), dt, nsteps, "lanczos", order=m)
+    H.sync()
+    assert rel(c.cpu().numpy(), ref) < TOL[prec]
+
+
+def test_lanczos_out_of_range_step_is_reported(tdse_lib):
+    """|T dt| far beyond what the Krylov space resolves: the step is not formed
+    and tdse_sync reports it; the context stays usable."""
+    lmax, n = 2, 40
+    E = inputs.energies(lmax, n)
+    H = tdse_lib.Hamiltonian(E, inputs.dipoles(lmax, n, 5), lmax, n, "fp64")
+    F = torch.from_numpy(inputs.field_samples(0.1, 0.5, 1e5, 1, 1)).cuda()
+    c = torch.from_numpy(inputs.random_state((lmax + 1) * n, 6)).cuda()
+    H.propagate(c, F, 1e5, 1, "lanczos", order=6)
+    with pytest.raises(tdse_lib.TDSEError):
+        H.sync()
+    F2 = torch.from_numpy(inputs.field_samples(0.1, 0.5, 0.05, 4, 1)).cuda()
+    c2 = torch.from_numpy(inputs.random_state((lmax + 1) * n, 6)).cuda()
+    H.propagate(c2, F2, 0.05, 4, "lanczos", order=6)
+    H.sync()
+    assert abs(float(torch.linalg.norm(c2)) - 1.0) < 1e-12
