@@ -437,16 +437,17 @@ def schemes_section(args):
 def uneven_section(args):
     """64 systems of different (lmax, n) (lmax 4..32, n 200..1500, each its own
     pulse) advanced together by tdse_group_propagate: RK4 amplitude-updates/s
-    with FP32 and float-float products after the ring-depth autotuner, the
-    product bandwidth, and the error on the two smallest members over the
-    timed window against the single-system FP64 path (itself checked against
-    the oracle by the tests)."""
+    with FP32, float-float and FP64 products after the ring-depth autotuner,
+    the product bandwidth (and for FP64, bound by the FP64 pipe, its FLOP
+    rate), and the error on the two smallest members over the timed window
+    against the single-system FP64 path (itself checked against the oracle by
+    the tests)."""
     import torch
     from paper_1201_6062_gb300 import inputs, tdse
     mem = inputs.uneven_batch(64)
     dt, W, K = 0.01, 2, 10
     t0 = 20.0
-    precs = ("fp32", "df32")
+    precs = ("fp32", "df32", "fp64")
     hams = {p: [] for p in precs}
     elems = 0
     small = sorted(range(len(mem)), key=lambda i: mem[i]["lmax"] * mem[i]["n"] ** 2)[:2]
@@ -497,6 +498,8 @@ def uneven_section(args):
         out[p] = {"value": amps / (ms / 1e3), "ms_per_step": ms, "product_gbs": 4 * elems * eb / (ms / 1e3) / 1e9,
                   "tuned_rows_per_stage_largest_bucket": rs, "tuned_ms_per_product": tune_ms,
                   "err_vs_fp64_max": err, "sampled_systems": small}
+        if p == "fp64":
+            out[p]["product_tflops"] = 4 * elems * 8 / (ms / 1e3) / 1e12     # 8 FP64 flops per dipole element
         g.close()
         for h in hams[p]:
             h.close()

@@ -62,15 +62,38 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
         fence_mbar_init();
     }
     __syncthreads();
+    const int s0 = cta_off[blockIdx.x], s1 = cta_off[blockIdx.x + 1];
+    const uint64_t pol = l2_evict_first_policy();
+    const uint64_t pol_x = l2_evict_last_policy();
+    // The dipole rows and the plan never change between launches: the producer
+    // starts the dipole copies of the first NS stages before waiting for the
+    // previous kernel (whose output, x, is copied only after the wait), so the
+    // ring fills while that kernel finishes.
+    int npre = 0;
+    if (warp == NW) {
+        for (int si = s0; si < s1 && npre < NS; ++si) {
+            const Seg sg = segs[si];
+            const SysDesc &S = sys[sg.sys];
+            const long long ld = S.ld;
+            const Elem *Ub = reinterpret_cast<const Elem *>(S.U) + (long long)sg.l * S.bstride;
+            for (int r = sg.i0; r < sg.i1 && npre < NS; r += RS) {
+                const int nr = min(RS, sg.i1 - r);
+                if (lane == 0) {
+                    const uint32_t bytes = (uint32_t)(nr * ld * (long long)sizeof(Elem));
+                    mbar_arrive_expect_tx(&full[npre], bytes + (uint32_t)(nr * 16));
+                    bulk_g2s(ring + (size_t)npre * stage, Ub + (long long)r * ld, bytes, &full[npre], pol);
+                }
+                __syncwarp();
+                ++npre;
+            }
+        }
+    }
     pdl_launch_dependents();
     pdl_wait();                            // inputs (x) come from the previous kernel
     volatile int *abort = &abort_flag;
-    const int s0 = cta_off[blockIdx.x], s1 = cta_off[blockIdx.x + 1];
 
     if (warp == NW) {
         // ---------------------------------------------------- producer warp
-        const uint64_t pol = l2_evict_first_policy();
-        const uint64_t pol_x = l2_evict_last_policy();
         int q = 0;
         bool ok = true;
         for (int si = s0; si < s1 && ok; ++si) {
@@ -90,10 +113,12 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     if (!w) { ok = false; break; }
                 }
                 if (lane == 0) {
-                    const uint32_t bytes = (uint32_t)(nr * ld * (long long)sizeof(Elem));
                     const uint32_t xbytes = (uint32_t)(nr * 16);
-                    mbar_arrive_expect_tx(&full[s], bytes + xbytes);
-                    bulk_g2s(ring + (size_t)s * stage, Ub + (long long)r * ld, bytes, &full[s], pol);
+                    if (q >= npre) {           // (stages q < npre: dipole rows already in flight)
+                        const uint32_t bytes = (uint32_t)(nr * ld * (long long)sizeof(Elem));
+                        mbar_arrive_expect_tx(&full[s], bytes + xbytes);
+                        bulk_g2s(ring + (size_t)s * stage, Ub + (long long)r * ld, bytes, &full[s], pol);
+                    }
                     bulk_g2s(&xs_raw[s][0], reinterpret_cast<const char *>(S.xq) + (base_l + r) * 16, xbytes, &full[s],
                              pol_x);
                 }
