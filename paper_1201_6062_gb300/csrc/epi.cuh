@@ -1,21 +1,54 @@
 // Per-amplitude epilogue of one stage (paper Sec. 4: H x = E x + f D x with
-// D x assembled from the row sums R and the column-partial slots P by dx_at;
-// App. B:
+// D x assembled from the row sums R and the column-partial slots P; App. B:
 // the RK4 stage and Taylor term combinations), all in FP64.  Used by the
-// separate epilogue kernel and, fused, by the ring mat-vec kernel.
+// epilogue kernel that follows each block product.
 #pragma once
 #include "kernels.h"
 
 namespace tdse {
 
-// kCG: read R and P around L1 (they were written by other CTAs of the same
-// launch and published with a fence + counter).
-template <class P, bool kCG>
-__device__ __forceinline__ void epi_amp(const SysDesc &S, long long a, const EpiArgs &A)
+// Inputs of one amplitude that no kernel of a call writes (its energy and
+// the slot range of its column partials): the epilogue kernel reads them
+// before it waits for the block product.
+struct EpiPre {
+    double e;
+    int m, i, b0, b1;
+};
+
+__device__ __forceinline__ EpiPre epi_pre(const SysDesc &S, long long a)
 {
-    const double2 dx = dx_at<kCG>(S, a);
+    EpiPre p;
+    p.m = (int)(a / S.n);
+    p.i = (int)(a - (long long)p.m * S.n);
+    p.e = S.E[a];
+    p.b0 = p.m >= 1 ? S.sb[p.m - 1] : 0;
+    p.b1 = p.m >= 1 ? S.sb[p.m] : 0;
+    return p;
+}
+
+// D x at amplitude a: the row sum (blocks below lmax) plus the column
+// partials of block m-1 in slot order; velocity gauge D x = i (R - sum P).
+__device__ __forceinline__ double2 epi_dx(const SysDesc &S, long long a, const EpiPre &p)
+{
+    double rr = 0.0, ri = 0.0, pr = 0.0, pi = 0.0;
+    if (p.m < S.lmax) {
+        const double2 r = S.R[a];
+        rr = r.x; ri = r.y;
+    }
+    for (int s = p.b0; s < p.b1; ++s) {
+        const double2 q = S.P[(long long)s * S.n + p.i];
+        pr += q.x; pi += q.y;
+    }
+    if (S.gauge == 0) return make_double2(rr + pr, ri + pi);
+    return make_double2(-(ri - pi), rr - pr);
+}
+
+template <class P>
+__device__ __forceinline__ void epi_amp(const SysDesc &S, long long a, const EpiArgs &A, const EpiPre &pre)
+{
+    const double2 dx = epi_dx(S, a, pre);
     const double dr = dx.x, di = dx.y;
-    const double e = S.E[a];
+    const double e = pre.e;
     double f;
     double2 xin;
     if (A.mode == EPI_RK4) {

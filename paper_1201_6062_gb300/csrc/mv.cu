@@ -268,13 +268,17 @@ __global__ void __launch_bounds__(256)
 epi_kernel(const SysDesc *__restrict__ sys, const int2 *__restrict__ blk, EpiArgs A)
 {
     pdl_launch_dependents();
-    pdl_wait();
+    // The plan, the descriptor, the energies and the slot ranges are the same
+    // for every launch of a call: read them before waiting for the product.
     const int2 bm = blk[blockIdx.x];
-    const SysDesc &S = sys[bm.x];
+    const SysDesc S = sys[bm.x];
     const long long a = (long long)bm.y + threadIdx.x;
-    if (a >= S.N) return;
+    const bool live = a < S.N;
+    const EpiPre pre = live ? epi_pre(S, a) : EpiPre{};
+    pdl_wait();
+    if (!live) return;
     if (A.kdev) A.k = *A.kdev;
-    epi_amp<P, false>(S, a, A);
+    epi_amp<P>(S, a, A, pre);
 }
 
 template <class P>
