@@ -61,9 +61,9 @@ typedef enum {
                            `taylor_order` = Krylov dimension m (1..32) products per
                            step, H frozen at the time `taylor_hold` selects, then
                            c <- |c| V exp(-i T dt) e_1 with T the Lanczos tridiagonal.
-                           A step with |T - sigma| |dt| > 4096 (sigma the centre
-                           of T's Gershgorin interval) is not formed: the state
-                           becomes invalid and the next tdse_sync fails.
+                           A step whose |dt| times the half-width of T's
+                           Gershgorin interval exceeds 4096 is not formed: the
+                           state becomes invalid and the next tdse_sync fails.
                            tdse_propagate / tdse_propagate_host only.              */
 } tdse_scheme;
 

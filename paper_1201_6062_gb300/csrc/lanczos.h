@@ -9,7 +9,7 @@ namespace tdse {
 // y_j = (exp(-i T dt) e_1)_j.
 constexpr int LZ_MAX_M = 32;       // Krylov dimension: one warp lane per index in lz_small
 constexpr int LZ_SCAL = 256;
-constexpr int LZ_SUBSTEP_MAX = 4096;   // bound on |T - sigma| |dt| handled by lz_small
+constexpr int LZ_SUBSTEP_MAX = 4096;   // bound on |dt| x the Gershgorin half-width of T (lz_small)
 // Bit of the context's device status word (beside kErrTimeout = 1): a Lanczos
 // step's small exponential was out of range.
 constexpr int kErrKrylov = 2;

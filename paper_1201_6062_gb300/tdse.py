@@ -196,7 +196,9 @@ class Hamiltonian:
 
     def propagate(self, c, field, dt, nsteps, scheme="rk4", order=4, hold=HOLD_LEFT, samples_per_step=1,
                   stream=None):
-        """Advance c (in place) over nsteps steps; returns c."""
+        """Advance c (in place) over nsteps steps; returns c.  Asynchronous on
+        the stream: device-side failures (a bounded wait that gave up, a
+        Lanczos step too long for its Krylov exponential) surface at sync()."""
         c = _dev_c(c, self.N)
         field = _dev_f64(field, self.nfield(nsteps, samples_per_step), "field")
         _check(_lib.tdse_propagate(self._h, _ptr(c), _ptr(field), int(samples_per_step), float(dt), int(nsteps),
