@@ -36,6 +36,25 @@ MUTANTS = [
     ("lanczos_three_term_recurrence",
      "if (j > 0) w[q] -= be[j] * V[(long)(j - 1) * 2 * N + q];", "(void)0;",
      lambda: pins.test_lanczos_full_krylov_space_is_the_exact_exponential()),
+    ("zero_energy_counted_as_bound",
+     "if (E[a] < 0.0) b += p; else io += p;", "if (E[a] <= 0.0) b += p; else io += p;",
+     lambda: pins.test_populations_partition_the_norm()),
+    ("eigenvector_rotation_sign",
+     "z[k * m + i] = c * z[k * m + i] - s * f;", "z[k * m + i] = c * z[k * m + i] + s * f;",
+     lambda: pins.test_tridiagonal_eigensolver_matches_numpy(7)),
+    ("rk4_last_stage_at_mid_step",
+     "orc_field_at(F, samples_per_step, k, 2), dt, work, NULL);",
+     "orc_field_at(F, samples_per_step, k, 1), dt, work, NULL);",
+     lambda: pins.test_convergence_orders_time_dependent_field()),
+    ("adjoint_forward_pass_last_stage_at_mid_step",
+     "orc_field_at(F, sps, k, 2), dt, work, NULL);", "orc_field_at(F, sps, k, 1), dt, work, NULL);",
+     lambda: pins.test_adjoint_matches_central_differences("rk4", 4, 2, 0)),
+    ("taylor_mid_hold_ignored",
+     "return orc_field_at(F, sps, k, hold ? 1 : 0);", "return orc_field_at(F, sps, k, 0);",
+     lambda: pins.test_convergence_orders_time_dependent_field()),
+    ("rkf_safety_factor",
+     "0.9 * pow(tol / err, 0.2)", "0.8 * pow(tol / err, 0.2)",
+     lambda: pins.test_rkf45_controller_matches_an_independent_simulation()),
 ]
 
 
