@@ -52,6 +52,18 @@ MUTANTS = [
     ("taylor_mid_hold_ignored",
      "return orc_field_at(F, sps, k, hold ? 1 : 0);", "return orc_field_at(F, sps, k, 0);",
      lambda: pins.test_convergence_orders_time_dependent_field()),
+    ("gauss_legendre_node",
+     "const double x1 = sqrt(5.0 - r) / 3.0", "const double x1 = sqrt(5.0 - r) / 3.1",
+     lambda: pins.test_vector_potential_gauss_legendre_matches_the_closed_form()),
+    ("vector_potential_sign",
+     "if (k > 0) A -= gl5(", "if (k > 0) A += gl5(",
+     lambda: pins.test_vector_potential_gauss_legendre_matches_the_closed_form()),
+    ("lanczos_diagonal_scale",
+     "a += vj[q] * w[q];     /* Re<v, w> */", "a += 0.5 * vj[q] * w[q];     /* Re<v, w> */",
+     lambda: pins.test_lanczos_full_krylov_space_is_the_exact_exponential()),
+    ("fehlberg_embedded_weight",
+     "2197.0 / 4104.0, -1.0 / 5.0, 0.0}", "2197.0 / 4104.0, -1.0 / 6.0, 0.0}",
+     lambda: pins.test_rkf45_tableau_satisfies_the_order_conditions()),
     ("rkf_safety_factor",
      "0.9 * pow(tol / err, 0.2)", "0.8 * pow(tol / err, 0.2)",
      lambda: pins.test_rkf45_controller_matches_an_independent_simulation()),
