@@ -406,56 +406,74 @@ void orc_adjoint(int lmax, int n, const double *E, const double *U, double *c,
 
 /*
  * Eigen-decomposition of a real symmetric tridiagonal matrix (diagonal d[m],
- * off-diagonal e[m], e[0..m-2] used) by the implicit QL iteration with Wilkinson shifts.
- * On return d holds the eigenvalues and z (m x m, row-major, z[i*m+k] = component i of
- * eigenvector k) the orthonormal eigenvectors.  Returns 0, or -1 if an eigenvalue needs
- * more than 60 iterations.
+ * off-diagonal e[m], e[0..m-2] used) by the cyclic Jacobi method: the matrix
+ * is written out densely as A, and each sweep visits every pair p < q once
+ * and applies the plane rotation J(p, q) that makes the (p, q) entry of
+ * J^T A J zero; the product of the rotations collects the eigenvectors.
+ * The rotation angle solves cot(2 phi) = (A_qq - A_pp) / (2 A_pq); of the
+ * two roots t = tan(phi) of t^2 + 2 theta t - 1 = 0 the one of smaller
+ * magnitude is taken (|phi| <= pi/4), which makes the sweeps converge.
+ * The sweeps stop when the off-diagonal mass sum_{p != q} A_pq^2 falls below
+ * (1e-17 |A|_F)^2 or is zero.  A tridiagonal matrix fills in under the
+ * rotations, so the whole m x m matrix is kept (m is a Krylov dimension,
+ * small).  On return d holds the eigenvalues (unsorted) and z (m x m,
+ * row-major, z[i*m+k] = component i of eigenvector k) the orthonormal
+ * eigenvectors.  Returns 0, or -1 if 100 sweeps do not converge.
  */
 int orc_tridiag_eig(int m, double *d, double *e, double *z)
 {
+    if (m <= 0) return 0;
+    double *A = (double *)calloc((size_t)m * m, sizeof(double));
+    double fro = 0.0;
+    for (int i = 0; i < m; ++i) {
+        A[(long)i * m + i] = d[i];
+        if (i + 1 < m) { A[(long)i * m + i + 1] = e[i]; A[(long)(i + 1) * m + i] = e[i]; }
+    }
+    for (long q = 0; q < (long)m * m; ++q) fro += A[q] * A[q];
+    const double floor2 = 1e-34 * fro;          /* (1e-17 |A|_F)^2 */
     for (int i = 0; i < m; ++i)
         for (int k = 0; k < m; ++k) z[i * m + k] = (i == k) ? 1.0 : 0.0;
-    if (m > 0) e[m - 1] = 0.0;
-    for (int l = 0; l < m; ++l) {
-        int iter = 0, mm;
-        do {
-            for (mm = l; mm < m - 1; ++mm) {
-                const double dd = fabs(d[mm]) + fabs(d[mm + 1]);
-                if (fabs(e[mm]) <= 1e-16 * dd) break;
-            }
-            if (mm != l) {
-                if (++iter > 60) return -1;
-                double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-                double r = hypot(g, 1.0);
-                g = d[mm] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
-                double s = 1.0, c = 1.0, p = 0.0;
-                int i;
-                for (i = mm - 1; i >= l; --i) {
-                    double f = s * e[i], b = c * e[i];
-                    r = hypot(f, g);
-                    e[i + 1] = r;
-                    if (r == 0.0) { d[i + 1] -= p; e[mm] = 0.0; break; }
-                    s = f / r;
-                    c = g / r;
-                    g = d[i + 1] - p;
-                    r = (d[i] - g) * s + 2.0 * c * b;
-                    p = s * r;
-                    d[i + 1] = g + p;
-                    g = c * r - b;
-                    for (int k = 0; k < m; ++k) {
-                        f = z[k * m + i + 1];
-                        z[k * m + i + 1] = s * z[k * m + i] + c * f;
-                        z[k * m + i] = c * z[k * m + i] - s * f;
-                    }
+    int sweep;
+    for (sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int k = 0; k < m; ++k)
+                if (i != k) off += A[(long)i * m + k] * A[(long)i * m + k];
+        if (off == 0.0 || off <= floor2) break;
+        for (int p = 0; p < m - 1; ++p) {
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = A[(long)p * m + q];
+                if (apq == 0.0) continue;
+                const double theta = (A[(long)q * m + q] - A[(long)p * m + p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                /* columns p and q of A J */
+                for (int k = 0; k < m; ++k) {
+                    const double akp = A[(long)k * m + p], akq = A[(long)k * m + q];
+                    A[(long)k * m + p] = cs * akp - sn * akq;
+                    A[(long)k * m + q] = sn * akp + cs * akq;
                 }
-                if (r == 0.0 && i >= l) continue;
-                d[l] -= p;
-                e[l] = g;
-                e[mm] = 0.0;
+                /* rows p and q of J^T (A J) */
+                for (int k = 0; k < m; ++k) {
+                    const double apk = A[(long)p * m + k], aqk = A[(long)q * m + k];
+                    A[(long)p * m + k] = cs * apk - sn * aqk;
+                    A[(long)q * m + k] = sn * apk + cs * aqk;
+                }
+                /* the rotation was chosen to annihilate this pair */
+                A[(long)p * m + q] = 0.0;
+                A[(long)q * m + p] = 0.0;
+                /* eigenvectors: z <- z J */
+                for (int k = 0; k < m; ++k) {
+                    const double vp = z[k * m + p], vq = z[k * m + q];
+                    z[k * m + p] = cs * vp - sn * vq;
+                    z[k * m + q] = sn * vp + cs * vq;
+                }
             }
-        } while (mm != l);
+        }
     }
-    return 0;
+    for (int i = 0; i < m; ++i) d[i] = A[(long)i * m + i];
+    free(A);
+    return sweep < 100 ? 0 : -1;
 }
 
 /*

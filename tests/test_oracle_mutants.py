@@ -40,7 +40,7 @@ MUTANTS = [
      "if (E[a] < 0.0) b += p; else io += p;", "if (E[a] <= 0.0) b += p; else io += p;",
      lambda: pins.test_populations_partition_the_norm()),
     ("eigenvector_rotation_sign",
-     "z[k * m + i] = c * z[k * m + i] - s * f;", "z[k * m + i] = c * z[k * m + i] + s * f;",
+     "z[k * m + q] = sn * vp + cs * vq;", "z[k * m + q] = -sn * vp + cs * vq;",
      lambda: pins.test_tridiagonal_eigensolver_matches_numpy(7)),
     ("rk4_last_stage_at_mid_step",
      "orc_field_at(F, samples_per_step, k, 2), dt, work, NULL);",
