@@ -606,8 +606,9 @@ void orc_vector_potential_sin2(double E0, double om, double ncyc, double t0, dou
  * the 5th-order solution) and the difference of the two combinations
  * estimates the local error.
  *
- * Step-size control (the paper fixes no rule; reading stated in the design
- * notes): the error of an attempt is err = |e|_2 / |c|_2 with
+ * Step-size control (the paper names the pair but fixes no rule for the step
+ * size, so this is a reading: the usual relative-error controller with
+ * Fehlberg's fifth-order exponent): the error of an attempt is err = |e|_2 / |c|_2 with
  * e = h sum (b5_i - b4_i) k_i.  The attempt is accepted when err <= tol or
  * when the step is at dt_min (h <= dt_min or the proposal dt <= dt_min: a
  * forced acceptance).  When the next step can no longer move t (tol

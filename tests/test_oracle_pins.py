@@ -342,7 +342,12 @@ def test_equal_matvec_counts_of_the_paper():
         elif r["scheme"] == "taylor":
             _, nmv = oracle.taylor(lmax, n, E, U, c0, F, r["dt"], nsteps, r["order"])
         else:
-            continue   # RKF 4(5) is not implemented (no tableau in the paper)
+            # a fixed step: dt_min = dt_max = dt and a tolerance every attempt meets
+            _, info = oracle.rkf45(lmax, n, E, U, c0, 0.0, nsteps * r["dt"], r["dt"], 1.0, field="const",
+                                   dt_min=r["dt"], dt_max=r["dt"])
+            assert info["rejected"] == 0 and info["accepted"] == nsteps
+            nmv = info["products"]
+        assert r["matvecs_per_step"] * nsteps == nmv
         assert abs(nmv / (nsteps * r["dt"]) - g["equal_matvec_comparison"]["matvecs_per_au"]) < 1e-9
 
 
