@@ -360,6 +360,18 @@ tdse_status tdse_profile_enable(tdse_ctx *ctx, int on);
 tdse_status tdse_profile_read(tdse_ctx *ctx, double *mv_ms, long *mv_launches, long *kernel_launches);
 
 /*
+ * Launch shape of the block product (Sec. 4.1: the rows of all stored blocks
+ * are split into one balanced contiguous range per work-group).  Reports the
+ * CTAs of one product launch, the ring CTAs the plan places on each SM (1:
+ * every CTA holds an SM alone; more when short rows of dipole blocks that
+ * stream from HBM leave shared memory for several rings), the threads per
+ * CTA, and whether rows stream through the bulk-copy ring (1) or per-thread
+ * loads (0).  Any output pointer may be NULL.  A bf16x3 context has no
+ * single-system product: ENOTSUP.  Errors: EINVAL, ENOTSUP.
+ */
+tdse_status tdse_plan_info(const tdse_ctx *ctx, int *ctas, int *ctas_per_sm, int *threads, int *ring);
+
+/*
  * tdse_populations_noalloc — the populations of tdse_populations for callers
  * that cannot allocate device memory when they need them (for example when
  * another framework's allocator already holds all device memory, or inside a
@@ -425,6 +437,15 @@ tdse_status tdse_group_sync(tdse_group *g, void *stream);
  * Errors: EINVAL, ECUDA, ETIMEOUT.
  */
 tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *best_ms, void *stream);
+
+/*
+ * tdse_group_plan_info — as tdse_plan_info, for bucket `bucket` of a group
+ * (0 <= bucket < *buckets); also reports the number of buckets, its members
+ * and the rows per ring stage its launches use.  Any output pointer may be
+ * NULL; with bucket = -1 only *buckets is written.  Errors: EINVAL.
+ */
+tdse_status tdse_group_plan_info(const tdse_group *g, int bucket, int *buckets, int *members, int *ctas,
+                                 int *ctas_per_sm, int *threads, int *ring, int *rows_per_stage);
 
 #ifdef __cplusplus
 }

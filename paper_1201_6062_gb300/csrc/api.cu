@@ -888,6 +888,28 @@ tdse_status tdse_profile_enable(tdse_ctx *ctx, int on)
     return TDSE_OK;
 }
 
+static void plan_shape(const MvPlan &mp, int *ctas, int *ctas_per_sm, int *threads, int *ring)
+{
+    if (ctas) *ctas = mp.grid;
+    if (ctas_per_sm) *ctas_per_sm = mp.cfg.tma ? mp.cfg.per_sm : 0;
+    if (threads) *threads = mp.cfg.BT;
+    if (ring) *ring = mp.cfg.tma;
+}
+
+tdse_status tdse_plan_info(const tdse_ctx *ctx, int *ctas, int *ctas_per_sm, int *threads, int *ring)
+{
+    g_err.clear();
+    if (!ctx) return fail(TDSE_EINVAL, "NULL context");
+    if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts have no single-system product");
+    plan_shape(ctx->plan, ctas, ctas_per_sm, threads, ring);
+    if (ctas_per_sm && !ctx->plan.cfg.tma) {
+        // per-thread-load plans: CTAs per SM follow from the grid over the SMs
+        const int sms = sm_count();
+        *ctas_per_sm = (ctx->plan.grid + sms - 1) / sms;
+    }
+    return TDSE_OK;
+}
+
 tdse_status tdse_profile_read(tdse_ctx *ctx, double *mv_ms, long *mv_launches, long *kernel_launches)
 {
     g_err.clear();
@@ -1493,6 +1515,25 @@ tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *bes
     if (chosen_rs) *chosen_rs = big_rs;
     if (best_ms) *best_ms = total;
     return tdse_group_sync(g, stream);
+}
+
+tdse_status tdse_group_plan_info(const tdse_group *g, int bucket, int *buckets, int *members, int *ctas,
+                                 int *ctas_per_sm, int *threads, int *ring, int *rows_per_stage)
+{
+    g_err.clear();
+    if (!g) return fail(TDSE_EINVAL, "NULL group");
+    if (buckets) *buckets = (int)g->buckets.size();
+    if (bucket == -1) return TDSE_OK;
+    if (bucket < 0 || bucket >= (int)g->buckets.size()) return fail(TDSE_EINVAL, "bucket %d out of range", bucket);
+    const GroupBucket &b = g->buckets[(size_t)bucket];
+    if (members) *members = (int)b.members.size();
+    plan_shape(b.plan, ctas, ctas_per_sm, threads, ring);
+    if (ctas_per_sm && !b.plan.cfg.tma) {
+        const int sms = sm_count();
+        *ctas_per_sm = (b.plan.grid + sms - 1) / sms;
+    }
+    if (rows_per_stage) *rows_per_stage = b.plan.cfg.tma ? (b.tuned_rs ? b.tuned_rs : b.plan.cfg.RS) : 0;
+    return TDSE_OK;
 }
 
 }  // extern "C"

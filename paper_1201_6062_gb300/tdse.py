@@ -53,6 +53,8 @@ _SIGS = {
     "tdse_group_create": ([_vp, _i, ctypes.POINTER(_vp)], _i),
     "tdse_group_destroy": ([_vp], None),
     "tdse_group_propagate": ([_vp, _vp, _vp, _i, _d, _l, _vp], _i),
+    "tdse_plan_info": ([_vp] + [ctypes.POINTER(_i)] * 4, _i),
+    "tdse_group_plan_info": ([_vp, _i] + [ctypes.POINTER(_i)] * 7, _i),
 }
 class _FieldFn(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("E0", ctypes.c_double), ("omega", ctypes.c_double),
@@ -249,6 +251,12 @@ class Hamiltonian:
         _check(_lib.tdse_profile_read(self._h, ctypes.byref(ms), ctypes.byref(nmv), ctypes.byref(nk)))
         return ms.value, nmv.value, nk.value
 
+    def plan_info(self):
+        """Launch shape of the block product: dict(ctas, ctas_per_sm, threads, ring)."""
+        v = [_i() for _ in range(4)]
+        _check(_lib.tdse_plan_info(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("ctas", "ctas_per_sm", "threads", "ring"), [x.value for x in v]))
+
     def adjoint(self, c0, field, dt, nsteps, weights, scheme="rk4", order=4, hold=HOLD_LEFT, samples_per_step=1,
                 checkpoint_every=64, stream=None):
         """Loss L = sum_a w_a |c_a(T)|^2 and dL/dfield by the discrete adjoint.
@@ -348,6 +356,18 @@ class Group:
 
     def sync(self, stream=None):
         _check(_lib.tdse_group_sync(self._g, _stream(stream)))
+
+    def plan_info(self):
+        """Per bucket: dict(members, ctas, ctas_per_sm, threads, ring, rows_per_stage)."""
+        nb = _i()
+        _check(_lib.tdse_group_plan_info(self._g, -1, ctypes.byref(nb), None, None, None, None, None, None))
+        out = []
+        for b in range(nb.value):
+            v = [_i() for _ in range(6)]
+            _check(_lib.tdse_group_plan_info(self._g, b, None, *[ctypes.byref(x) for x in v]))
+            out.append(dict(zip(("members", "ctas", "ctas_per_sm", "threads", "ring", "rows_per_stage"),
+                                [x.value for x in v])))
+        return out
 
     def tune(self, reps=3, stream=None):
         """Autotune the ring-stage depth of every bucket; returns (rows per
