@@ -388,7 +388,11 @@ tdse_status tdse_plan_info(const tdse_ctx *ctx, int *ctas, int *ctas_per_sm, int
  * reads, but calls whose kernels overlap on the GPU (different streams, no
  * ordering between them) race on it and must be serialised by the caller.
  * The first call on each device resolves the array's device address with
- * that device current; make that first call before any stream capture.
+ * that device current.  CUDA loads device code lazily by default, so that
+ * first call is also when the 384 KB array is placed in device memory: make
+ * it while the device still has that much free (before another allocator
+ * reserves the rest) and before any stream capture.  After cudaDeviceReset
+ * the next call on that device is a first call again.
  * Asynchronous on `stream`.  Errors: EINVAL, ECUDA.
  */
 tdse_status tdse_populations_noalloc(const double *c, const double *energies, int lmax, int n, int B,
@@ -437,6 +441,36 @@ tdse_status tdse_group_sync(tdse_group *g, void *stream);
  * Errors: EINVAL, ECUDA, ETIMEOUT.
  */
 tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *best_ms, void *stream);
+
+/*
+ * Failure detection.
+ *
+ * tdse_set_device_memory_limit caps the device memory that all contexts and
+ * groups of this library hold together (bytes; 0 removes the cap).  A call
+ * that would allocate beyond it fails with TDSE_ENOMEM, as when cudaMalloc
+ * itself fails, and leaves what it allocated before to its context.  It lets
+ * a caller bound the library's footprint beside another framework's
+ * allocator, and lets tests make an allocation fail without filling the GPU.
+ * tdse_device_memory_in_use reports the bytes held now.  The fixed scratch of
+ * tdse_populations_noalloc is not counted.  Errors: EINVAL.
+ *
+ * Every propagating call (tdse_propagate, _host, _batch, tdse_adjoint,
+ * tdse_group_propagate) scans its field samples on the device; a NaN or
+ * infinite sample sets a bit of the status word, and the next tdse_sync
+ * (tdse_group_sync) reports TDSE_EINVAL (the host-buffer entry point checks
+ * on the host and fails at once).
+ *
+ * tdse_inject_wait_timeout is a test hook for the timeout path: it runs, on
+ * `stream`, one CTA that streams a few bulk copies of the context's energies
+ * through a two-stage ring with the same bounded waits the product kernels
+ * use, then waits for one stage that nothing arms.  That wait gives up after
+ * timeout_ns (1e3..1e9), the CTA lets its copies in flight land, and the
+ * next tdse_sync reports TDSE_ETIMEOUT; the context stays usable.
+ * Errors: EINVAL, ENOTSUP (bf16x3), ECUDA.
+ */
+tdse_status tdse_set_device_memory_limit(long long bytes);
+long long tdse_device_memory_in_use(void);
+tdse_status tdse_inject_wait_timeout(tdse_ctx *ctx, long timeout_ns, void *stream);
 
 /*
  * tdse_group_plan_info — as tdse_plan_info, for bucket `bucket` of a group

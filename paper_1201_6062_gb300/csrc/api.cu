@@ -2,6 +2,7 @@
 // Host orchestration only: argument checks, device storage, the work plan and
 // the launch sequence.  Every arithmetic step runs in the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -47,24 +48,52 @@ tdse_status set_error(tdse_status s, const char *msg)
 }
 }  // namespace tdse
 
-#define CUDA_TRY(call)                                                                           \
-    do {                                                                                         \
-        cudaError_t e_ = (call);                                                                 \
-        if (e_ != cudaSuccess) return fail(TDSE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+// A failed device allocation is TDSE_ENOMEM, any other CUDA failure TDSE_ECUDA.
+static tdse_status cuda_status(cudaError_t e)
+{
+    return e == cudaErrorMemoryAllocation ? TDSE_ENOMEM : TDSE_ECUDA;
+}
+
+#define CUDA_TRY(call)                                                                                    \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return fail(cuda_status(e_), "%s: %s", #call, cudaGetErrorString(e_));     \
     } while (0)
+
+// Device memory the library's contexts and groups hold, and the optional cap
+// on it (tdse_set_device_memory_limit; 0: none).
+static std::atomic<long long> g_dev_bytes{0};
+static std::atomic<long long> g_dev_limit{0};
 
 // Device memory owned by a context or group; freed by the destructor.
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
-    ~DevBuf() { if (p) cudaFree(p); }
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) {
+            cudaFree(p);
+            g_dev_bytes -= (long long)bytes;
+        }
+        p = nullptr;
+        bytes = 0;
+    }
     cudaError_t ensure(size_t nbytes)
     {
         if (nbytes <= bytes && p) return cudaSuccess;
-        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
-        cudaError_t e = cudaMalloc(&p, nbytes ? nbytes : 16);
-        if (e == cudaSuccess) bytes = nbytes;
-        return e;
+        release();
+        const size_t want = nbytes ? nbytes : 16;
+        const long long cap = g_dev_limit.load();
+        if (cap > 0 && g_dev_bytes.load() + (long long)want > cap) return cudaErrorMemoryAllocation;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = want;
+        g_dev_bytes += (long long)want;
+        return cudaSuccess;
     }
     template <class T> T *as() const { return reinterpret_cast<T *>(p); }
 };
@@ -149,7 +178,23 @@ static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std:
         // more CTAs only add column-partial slots and per-CTA overhead.
         long long ubytes = 0;
         for (size_t q = 0; q < n.size(); ++q) ubytes += (long long)lmax[q] * n[q] * n[q] * elem_bytes(prec);
-        mp.cfg.per_sm = ubytes >= (64LL << 20) ? tdse::mvt_ctas_per_sm(prec, mp.cfg) : 1;
+        mp.cfg.per_sm = 1;
+        if (ubytes >= (64LL << 20)) {
+            // Rows per stage and resident CTAs trade against each other (a
+            // deeper stage needs more registers, which can leave room for
+            // fewer CTAs): take the depth with the most rows in flight per SM,
+            // the deeper one on a tie.
+            int best_rs = mp.cfg.RS, best_occ = 0;
+            for (int rs = mp.cfg.RS; rs >= 1; rs /= 2) {
+                tdse::MvCfg c = mp.cfg;
+                if (!tdse::mvt_rs_valid(prec, c, rs, ldmax)) continue;
+                c.RS = rs;
+                const int occ = tdse::mvt_ctas_per_sm(prec, c);
+                if (occ * rs > best_occ * best_rs || best_occ == 0) { best_occ = occ; best_rs = rs; }
+            }
+            mp.cfg.RS = best_rs;
+            mp.cfg.per_sm = best_occ > 0 ? best_occ : 1;
+        }
         G = sm_count() * mp.cfg.per_sm;
     } else {
         if (!tdse::mv_config(prec, nmax, &mp.cfg)) return fail(TDSE_ENOTSUP, "n=%d exceeds the supported maximum", nmax);
@@ -384,7 +429,7 @@ tdse_status tdse_create(const double *energies, const double *dipole_blocks, int
 #define CTRY(call)                                                                                \
     do {                                                                                          \
         cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess) return bail(fail(TDSE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_))); \
+        if (e_ != cudaSuccess) return bail(fail(cuda_status(e_), "%s: %s", #call, cudaGetErrorString(e_))); \
     } while (0)
     // Dipole blocks in the storage format of the precision (converted on the host).
     const size_t ubytes = (size_t)(lmax > 0 ? lmax : 1) * (size_t)c->bstride * eb;
@@ -528,6 +573,7 @@ tdse_status tdse_hmatvec(tdse_ctx *ctx, double f, const double *x, double *y, in
     if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
     if (!aligned16(x) || !aligned16(y)) return fail(TDSE_EINVAL, "x and y must be 16-byte aligned");
     if (x == y) return fail(TDSE_EINVAL, "x and y must not alias");
+    if (!std::isfinite(f)) return fail(TDSE_EINVAL, "the field value is not finite");
     cudaStream_t s = (cudaStream_t)stream;
     SysDesc d = ctx->desc;
     d.x = (double2 *)const_cast<double *>(x);
@@ -668,6 +714,9 @@ tdse_status tdse_propagate(tdse_ctx *ctx, double *c, const double *field, int sa
     tdse_status st = check_prop_args(ctx, c, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold);
     if (st != TDSE_OK) return st;
     if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts serve tdse_propagate_batch only");
+    CUDA_TRY(tdse::launch_field_check(field, (long long)samples_per_step * nsteps + 1, ctx->errw.as<int>(),
+                                      (cudaStream_t)stream));
+    ctx->launches += 1;
     return propagate_impl(ctx, c, field, samples_per_step, dt, nsteps, scheme, taylor_order, taylor_hold,
                           (cudaStream_t)stream);
 }
@@ -785,6 +834,8 @@ tdse_status tdse_propagate_host(tdse_ctx *ctx, double *c_host, const double *fie
     tdse_status st = check_prop_args(ctx, ctx->hc.as<double>(), ctx->hfield.as<double>(), samples_per_step, dt, nsteps,
                                      scheme, taylor_order, taylor_hold);
     if (st != TDSE_OK) return st;
+    for (size_t q = 0; q < fb / sizeof(double); ++q)
+        if (!std::isfinite(field_host[q])) return fail(TDSE_EINVAL, "field sample %ld is not finite", (long)q);
     st = propagate_impl(ctx, ctx->hc.as<double>(), ctx->hfield.as<double>(), samples_per_step, dt, nsteps, scheme,
                         taylor_order, taylor_hold, s);
     if (st != TDSE_OK) return st;
@@ -830,6 +881,20 @@ tdse_status tdse_vector_potential_sin2(double E0, double omega, double cycles, d
     return TDSE_OK;
 }
 
+// The failure a nonzero device status word reports (its bits: kErrTimeout,
+// kErrKrylov, kErrField); the results since the last check are invalid.
+static tdse_status status_word_error(int w)
+{
+    if (w & tdse::kErrTimeout)
+        return fail(TDSE_ETIMEOUT, "a bounded device-side wait gave up (status word 0x%x); the results of the "
+                                   "calls since the last check are invalid", w);
+    if (w & tdse::kErrField)
+        return fail(TDSE_EINVAL, "a field sample is NaN or infinite (status word 0x%x); the state is invalid", w);
+    return fail(TDSE_EINVAL, "a Lanczos step had |T dt| beyond %d or a non-finite Krylov matrix (status word "
+                             "0x%x): dt is too long for this Hamiltonian, and the state is invalid",
+                tdse::LZ_SUBSTEP_MAX, w);
+}
+
 tdse_status tdse_sync(tdse_ctx *ctx, void *stream)
 {
     if (!ctx) return fail(TDSE_EINVAL, "NULL context");
@@ -839,12 +904,7 @@ tdse_status tdse_sync(tdse_ctx *ctx, void *stream)
     CUDA_TRY(cudaMemcpy(&w, ctx->errw.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (w) {
         CUDA_TRY(cudaMemset(ctx->errw.p, 0, sizeof(int)));
-        if (w & tdse::kErrTimeout)
-            return fail(TDSE_ETIMEOUT, "a bounded device-side wait gave up (status word 0x%x); the results of the "
-                                       "calls since the last check are invalid", w);
-        return fail(TDSE_EINVAL, "a Lanczos step had |T dt| beyond %d or a non-finite Krylov matrix (status word "
-                                 "0x%x): dt is too long for this Hamiltonian, and the state is invalid",
-                    tdse::LZ_SUBSTEP_MAX, w);
+        return status_word_error(w);
     }
     return TDSE_OK;
 }
@@ -997,6 +1057,8 @@ tdse_status tdse_propagate_batch(tdse_ctx *ctx, double *c, const double *field, 
     cudaStream_t s = (cudaStream_t)stream;
     const long long N = ctx->N;
     const long S = (long)samples_per_step * nsteps + 1;
+    CUDA_TRY(tdse::launch_field_check(field, (long long)B * S, ctx->errw.as<int>(), s));
+    ctx->launches += 1;
     if (scheme == TDSE_LANCZOS && (ctx->prec == TDSE_BF16X3 || ctx->prec == TDSE_FP32))
         return fail(TDSE_ENOTSUP, "batched Lanczos runs on FP64 / float-float contexts only");
     if (ctx->prec == TDSE_BF16X3) {
@@ -1087,6 +1149,8 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
     if (checkpoint_every < 1) return fail(TDSE_EINVAL, "checkpoint_every must be >= 1");
     if (c_final && !aligned16(c_final)) return fail(TDSE_EINVAL, "c_final must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(tdse::launch_field_check(field, (long long)samples_per_step * nsteps + 1, ctx->errw.as<int>(), s));
+    ctx->launches += 1;
     const int sps = samples_per_step;
     const bool rk4 = scheme == TDSE_RK4;
     const int order = rk4 ? 4 : taylor_order;
@@ -1402,6 +1466,10 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const dou
         if (!aligned16(c_ptrs[i])) return fail(TDSE_EINVAL, "c_ptrs[%d] must be 16-byte aligned", i);
     }
     cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) {
+        CUDA_TRY(tdse::launch_field_check(field_ptrs[i], (long long)samples_per_step * nsteps + 1, g->errw.as<int>(), s));
+        g->launches += 1;
+    }
     if (g->stage_pending) CUDA_TRY(cudaEventSynchronize(g->stage_ev));
     for (int i = 0; i < count; ++i) {
         g->stage[i] = g->desc[i];
@@ -1451,7 +1519,7 @@ tdse_status tdse_group_sync(tdse_group *g, void *stream)
     CUDA_TRY(cudaMemcpy(&w, g->errw.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (w) {
         CUDA_TRY(cudaMemset(g->errw.p, 0, sizeof(int)));
-        return fail(TDSE_ETIMEOUT, "a bounded device-side wait gave up (status word 0x%x)", w);
+        return status_word_error(w);
     }
     return TDSE_OK;
 }
@@ -1515,6 +1583,28 @@ tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *bes
     if (chosen_rs) *chosen_rs = big_rs;
     if (best_ms) *best_ms = total;
     return tdse_group_sync(g, stream);
+}
+
+tdse_status tdse_set_device_memory_limit(long long bytes)
+{
+    g_err.clear();
+    if (bytes < 0) return fail(TDSE_EINVAL, "the limit must be >= 0");
+    g_dev_limit = bytes;
+    return TDSE_OK;
+}
+
+long long tdse_device_memory_in_use(void) { return g_dev_bytes.load(); }
+
+tdse_status tdse_inject_wait_timeout(tdse_ctx *ctx, long timeout_ns, void *stream)
+{
+    g_err.clear();
+    if (!ctx) return fail(TDSE_EINVAL, "NULL context");
+    if (timeout_ns < 1000 || timeout_ns > 1000000000L) return fail(TDSE_EINVAL, "timeout_ns must be in 1e3..1e9");
+    if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts have no product scratch");
+    CUDA_TRY(tdse::launch_inject_wait(ctx->E.as<double>(), (long long)sizeof(double) * ctx->N, ctx->errw.as<int>(),
+                                      timeout_ns, ctx->R.as<double>(), (cudaStream_t)stream));
+    ctx->launches += 1;
+    return TDSE_OK;
 }
 
 tdse_status tdse_group_plan_info(const tdse_group *g, int bucket, int *buckets, int *members, int *ctas,

@@ -140,4 +140,14 @@ struct SmallArgs {
 bool small_fits(int prec, int lmax, int n, int ld, long long N);
 cudaError_t launch_small(int prec, const SmallArgs &A, cudaStream_t stream);
 
+// Failure detection (check.cu).  launch_field_check sets kErrField in *err if
+// any of F[0, count) is NaN or infinite.  launch_inject_wait runs a one-CTA
+// miniature of the product's copy ring whose last stage is never armed, so
+// its bounded wait runs out after timeout_ns and kErrTimeout is set (a test
+// hook); the copies read src[0, min(6*512, src_bytes)) and one double is
+// written to sink.
+cudaError_t launch_field_check(const double *F, long long count, int *err, cudaStream_t stream);
+cudaError_t launch_inject_wait(const double *src, long long src_bytes, int *err, long long timeout_ns, double *sink,
+                               cudaStream_t stream);
+
 }  // namespace tdse

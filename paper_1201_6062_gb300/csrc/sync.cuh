@@ -5,10 +5,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "wait.h"
+
 namespace tdse {
 
-// Device status word bits.
+// Device status word bits (bit 2, kErrKrylov, is the Lanczos step's).
 constexpr int kErrTimeout = 1;
+constexpr int kErrField = 4;      // a field sample is NaN or infinite
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -63,16 +66,7 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort,
                                                   uint64_t timeout_ns)
 {
-    if (mbar_test(bar, parity)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    while (true) {
-        if (*abort) return false;
-        if (mbar_test(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > timeout_ns) {
-            *abort = 1;
-            return false;
-        }
-    }
+    return wait_bounded([&] { return mbar_test(bar, parity); }, [] { return globaltimer_ns(); }, abort, timeout_ns);
 }
 
 // L2 policy for data read exactly once per pass (the dipole blocks).

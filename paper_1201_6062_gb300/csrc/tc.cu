@@ -230,6 +230,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
     __shared__ __align__(8) uint64_t empty[TST];
     __shared__ __align__(8) uint64_t acc_full[2];
     __shared__ __align__(8) uint64_t acc_empty[2];
+    __shared__ __align__(8) uint64_t mma_drain;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ int issued, consumed;
@@ -250,6 +251,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
             mbar_init(&acc_full[a], 1);
             mbar_init(&acc_empty[a], EPI_WARPS);
         }
+        mbar_init(&mma_drain, 1);
         abort_flag = 0;
         issued = 0;
         consumed = 0;
@@ -395,6 +397,18 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
         atomicOr(A.err, kErrTimeout);
     }
     if (warp == 1) {
+        if (*abort) {
+            // After an abort the epilogue no longer waits for the last
+            // accumulators, so products already issued may still write tensor
+            // memory: a commit tracks every earlier tcgen05.mma of the issuing
+            // thread; free the columns only once it has arrived.
+            if (lane == 0) {
+                mma_commit(&mma_drain);
+                volatile int never = 0;
+                mbar_wait_bounded(&mma_drain, 0u, &never, TC_WAIT_NS);
+            }
+            __syncwarp();
+        }
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
     }

@@ -54,6 +54,9 @@ _SIGS = {
     "tdse_group_destroy": ([_vp], None),
     "tdse_group_propagate": ([_vp, _vp, _vp, _i, _d, _l, _vp], _i),
     "tdse_plan_info": ([_vp] + [ctypes.POINTER(_i)] * 4, _i),
+    "tdse_set_device_memory_limit": ([ctypes.c_longlong], _i),
+    "tdse_device_memory_in_use": ([], ctypes.c_longlong),
+    "tdse_inject_wait_timeout": ([_vp, _l, _vp], _i),
     "tdse_group_plan_info": ([_vp, _i] + [ctypes.POINTER(_i)] * 7, _i),
 }
 class _FieldFn(ctypes.Structure):
@@ -119,6 +122,16 @@ def _dev_f64(t, n, name):
     if n is not None and t.numel() != n:
         raise ValueError("%s has %d samples, expected %d" % (name, t.numel(), n))
     return t
+
+
+def set_device_memory_limit(nbytes):
+    """Cap the device memory all contexts and groups hold together (0: no cap);
+    allocations beyond it fail with ENOMEM."""
+    _check(_lib.tdse_set_device_memory_limit(int(nbytes)))
+
+
+def device_memory_in_use():
+    return int(_lib.tdse_device_memory_in_use())
 
 
 def vector_potential_sin2(E0, omega, cycles, t0, h, nsamples, out=None, stream=None):
@@ -250,6 +263,10 @@ class Hamiltonian:
         ms, nmv, nk = _d(), _l(), _l()
         _check(_lib.tdse_profile_read(self._h, ctypes.byref(ms), ctypes.byref(nmv), ctypes.byref(nk)))
         return ms.value, nmv.value, nk.value
+
+    def inject_wait_timeout(self, timeout_ns, stream=None):
+        """Test hook: one bounded device wait runs out after timeout_ns; the next sync() raises ETIMEOUT."""
+        _check(_lib.tdse_inject_wait_timeout(self._h, int(timeout_ns), _stream(stream)))
 
     def plan_info(self):
         """Launch shape of the block product: dict(ctas, ctas_per_sm, threads, ring)."""

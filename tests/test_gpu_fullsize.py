@@ -8,7 +8,8 @@
   has 8 x 4 x 16 = 512 tiles, 3.4 per SM.
 - A ring plan places several CTAs on one SM only when its dipole blocks
   stream from HBM (64 MB or more) and its rows are short enough for several
-  rings to share an SM's shared memory.
+  rings (and their consumers' registers) to share an SM; the plan then picks
+  the rows per ring stage that keep the most rows in flight per SM.
 - The adjoint workload (lmax=15, n=500, 4095 RK4 steps of dt 0.01, 4096
   step-grid field samples, loss = bound-state population, checkpoints every
   64 steps), against the oracle's FP64 adjoint and central differences.
@@ -73,8 +74,8 @@ def system(lmax, n, seed, dt, nsteps):
     return lmax, n, E, U, F, c0
 
 
-@pytest.mark.parametrize("prec,lmax,n", [("fp32", 80, 500), ("fp32", 130, 300), ("df32", 93, 300),
-                                         ("df32", 40, 450), ("fp64", 93, 300)])
+@pytest.mark.parametrize("prec,lmax,n", [("fp32", 80, 500), ("fp32", 190, 300), ("df32", 140, 250),
+                                         ("df32", 100, 300), ("df32", 45, 450), ("fp64", 100, 300)])
 def test_streamed_short_rows_take_several_ring_ctas_per_sm(tdse_lib, prec, lmax, n):
     dt, nsteps = 0.02, 3
     ub = {"fp64": 8, "df32": 8, "fp32": 4}[prec]
@@ -95,6 +96,7 @@ def test_streamed_short_rows_take_several_ring_ctas_per_sm(tdse_lib, prec, lmax,
 @pytest.mark.parametrize("prec,shapes", [
     ("fp32", [(60, 250), (70, 300), (80, 280), (65, 260), (9, 1200)]),
     ("df32", [(40, 250), (45, 300), (50, 280), (42, 260), (6, 900)]),
+    ("df32", [(60, 200), (70, 250), (80, 230), (65, 240), (3, 1400)]),
 ])
 def test_group_buckets_with_several_ring_ctas_per_sm(tdse_lib, prec, shapes):
     dt, nsteps = 0.02, 4
@@ -150,11 +152,15 @@ def test_adjoint_workload_matches_the_oracle_adjoint(tdse_lib, adjoint_case, pre
     assert np.all(np.abs(g[idx] - a["g_ref"][idx]) <= 1e-10 * np.abs(a["g_ref"][idx]) + 1e-12 * scale)
 
 
-def test_adjoint_workload_matches_central_differences(tdse_lib, adjoint_case):
-    """h = 1e-6 on 16 samples from default_rng(5), each entry against its own
-    difference quotient.  The loss (~1) carries a rounding error of a few
-    1e-16, so the quotient is good to about 1e-16 / h = 1e-10 absolute; the
-    truncation error h^2 L''' / 6 is far below that."""
+@pytest.mark.parametrize("h,floor", [(1e-3, 2e-11), (1e-6, 1e-8)])
+def test_adjoint_workload_matches_central_differences(tdse_lib, adjoint_case, h, floor):
+    """Central differences of the GPU forward pass on 16 samples from
+    default_rng(5), each entry against its own quotient: |fd - g| <= 1e-6 |fd|
+    + floor.  The floor is the quotient's own rounding noise: after 4095
+    steps the loss (~1) carries a rounding error of up to about 2e-14
+    (measured from second differences), which the quotient divides by 2h:
+    1e-11 at h = 1e-3, 1e-8 at h = 1e-6.  The truncation error (h^2 / 6 times
+    the third derivative) stays below 1e-11 at h = 1e-3."""
     a = adjoint_case
     H = tdse_lib.Hamiltonian(a["E"], a["U"], a["lmax"], a["n"], "fp64")
     c0d = torch.from_numpy(a["c0"]).cuda()
@@ -168,11 +174,10 @@ def test_adjoint_workload_matches_central_differences(tdse_lib, adjoint_case):
         return float(torch.sum(wd * (c.real ** 2 + c.imag ** 2)).item())
 
     idx = np.random.default_rng(5).choice(a["F"].size, 16, replace=False)
-    h = 1e-6
     for m in idx:
         Fp, Fm = a["F"].copy(), a["F"].copy()
         Fp[m] += h
         Fm[m] -= h
         fd = (loss(Fp) - loss(Fm)) / (2 * h)
-        assert abs(fd - g[m]) <= 1e-6 * abs(fd) + 1e-9, (int(m), fd, g[m])
+        assert abs(fd - g[m]) <= 1e-6 * abs(fd) + floor, (int(m), fd, g[m])
     H.close()
