@@ -142,7 +142,16 @@ struct PolF64 {
         fmax_(re, im, u, x);
     }
     static __device__ __forceinline__ Comp rdone(RowAcc a, Sigma) { return a; }
-    template <int K> static __device__ __forceinline__ Sigma sigma(const XV *, float) { return 0; }
+    template <int K> static __device__ __forceinline__ Sigma rsigma(float, float) { return 0; }
+    // Row sums are reduced across threads, column sums run over a segment,
+    // both in the plain accumulator.
+    using RComp = Comp;
+    static __device__ __forceinline__ RComp radd(RComp a, RComp b) { return add_fast(a, b); }
+    static __device__ __forceinline__ RComp rshfl(RComp a, int m) { return shfl(a, m); }
+    static __device__ __forceinline__ double rto_double(RComp a, Sigma) { return to_double(a); }
+    using CRun = Comp;
+    static __device__ __forceinline__ CRun czero() { return zero(); }
+    static __device__ __forceinline__ double cto_double(CRun a, Sigma) { return to_double(a); }
     // Column sums: per-chunk partials folded into the running sum.
     template <int K> static __device__ __forceinline__ Sigma csigma(float, float) { return 0; }
     static __device__ __forceinline__ float xabs(const XV &x) { return fmaxf(fabsf((float)x.re), fabsf((float)x.im)); }
@@ -199,7 +208,16 @@ struct PolF32 {
         fmax_(re, im, u, x);
     }
     static __device__ __forceinline__ Comp rdone(RowAcc a, Sigma) { return a; }
-    template <int K> static __device__ __forceinline__ Sigma sigma(const XV *, float) { return 0; }
+    template <int K> static __device__ __forceinline__ Sigma rsigma(float, float) { return 0; }
+    // Row sums are reduced across threads, column sums run over a segment,
+    // both in the plain accumulator.
+    using RComp = Comp;
+    static __device__ __forceinline__ RComp radd(RComp a, RComp b) { return add_fast(a, b); }
+    static __device__ __forceinline__ RComp rshfl(RComp a, int m) { return shfl(a, m); }
+    static __device__ __forceinline__ double rto_double(RComp a, Sigma) { return to_double(a); }
+    using CRun = Comp;
+    static __device__ __forceinline__ CRun czero() { return zero(); }
+    static __device__ __forceinline__ double cto_double(CRun a, Sigma) { return to_double(a); }
     // Column sums: per-chunk partials folded into the running sum.
     template <int K> static __device__ __forceinline__ Sigma csigma(float, float) { return 0; }
     static __device__ __forceinline__ float xabs(const XV &x) { return fmaxf(fabsf((float)x.re), fabsf((float)x.im)); }
@@ -247,16 +265,17 @@ struct PolDF32 {
     }
     static __device__ __forceinline__ Comp add(Comp a, Comp b) { return df_add(a, b); }
     static __device__ __forceinline__ Comp add_fast(Comp a, Comp b) { return df_add_lazy(a, b); }
-    // Short row sums (K products of |u| <= umax, |v| <= xmax): an offset
-    // accumulator.  T starts at sigma, a power of two >= 2 K umax xmax, so every
-    // partial sum keeps T within a factor two of sigma; then T' = fl(T + uh vh)
-    // changes by exactly d = T' - T (Sterbenz), and fma(uh, vh, -d) recovers
-    // the part of the product that T could not hold (to 2^-24 of ulp(T)).  The
+    // Short sums (K products of |u| <= umax, |v| <= xmax): an offset
+    // accumulator.  sigma is a power of two >= 4 K umax xmax and T starts at
+    // 1.5 sigma, so every partial sum keeps T inside [sigma, 2 sigma), where
+    // floats are evenly spaced by sigma 2^-23.  T' = fl(T + uh vh) changes by
+    // exactly d = T' - T (Sterbenz), and fma(uh, vh, -d) recovers the part of
+    // the product that T could not hold (to 2^-24 of the spacing).  The
     // low-order terms go straight into L.  6 FP32 operations per product
-    // instead of the 12 of df_fma; the sum is (T - sigma) + L.
+    // instead of the 12 of df_fma; the sum is (T - 1.5 sigma) + L.
     struct RowAcc { float T, L; };
     using Sigma = float;
-    static __device__ __forceinline__ RowAcc rzero(Sigma s) { return RowAcc{s, 0.f}; }
+    static __device__ __forceinline__ RowAcc rzero(Sigma s) { return RowAcc{1.5f * s, 0.f}; }
     static __device__ __forceinline__ void racc(RowAcc &a, df u, df v)
     {
         const float t = __fmaf_rn(u.h, v.h, a.T);
@@ -272,35 +291,51 @@ struct PolDF32 {
         racc(re, u, x.re);
         racc(im, u, x.im);
     }
-    static __device__ __forceinline__ Comp rdone(RowAcc a, Sigma s) { return df{__fsub_rn(a.T, s), a.L}; }
-    // Column sums over at most K rows with |x| <= xmax: the same offset
-    // accumulator, folded into a float-float running sum after each chunk.
-    template <int K> static __device__ __forceinline__ Sigma csigma(float xmax, float umax)
+    // A finished accumulator as a whole number k of steps sigma 2^-23 above
+    // 1.5 sigma plus its low word.  Within one binade the bit patterns of two
+    // floats differ by their distance in steps, so k is exact; |k| <= 2^21, and
+    // sums of up to 2^9 such k stay exact in 32-bit integers.  Sums of these
+    // pairs (across the threads of a row, or over the chunks of a column) are
+    // an integer add and an FP32 add, instead of a float-float addition.
+    struct RComp { int k; float L; };
+    static __device__ __forceinline__ RComp rdone(RowAcc a, Sigma s)
+    {
+        return RComp{__float_as_int(a.T) - __float_as_int(1.5f * s), a.L};
+    }
+    static __device__ __forceinline__ RComp radd(RComp a, RComp b) { return RComp{a.k + b.k, __fadd_rn(a.L, b.L)}; }
+    static __device__ __forceinline__ RComp rshfl(RComp a, int m)
+    {
+        return RComp{__shfl_xor_sync(0xffffffffu, a.k, m), __shfl_xor_sync(0xffffffffu, a.L, m)};
+    }
+    static __device__ __forceinline__ double rto_double(RComp a, Sigma s)
+    {
+        return (double)a.k * ((double)s * 0x1p-23) + (double)a.L;
+    }
+    // sigma for sums of K products with |x| <= xmax (every thread of a CTA
+    // takes the same, so their k count the same steps): a power of two >= 4 K
+    // umax xmax, at least 2^-100.
+    template <int K> static __device__ __forceinline__ Sigma rsigma(float xmax, float umax)
     {
         const float bound = 4.f * (float)K * umax * xmax;
         if (!(bound > 0.f)) return 0x1p-100f;
         int e;
-        frexpf(bound, &e);
-        return ldexpf(1.f, e > -100 ? e : -100);
-    }
-    static __device__ __forceinline__ float xabs(const XV &x) { return fmaxf(fabsf(x.re.h), fabsf(x.im.h)); }
-    static __device__ __forceinline__ void cfold(Comp &run, RowAcc &a, Sigma s)
-    {
-        run = df_add(run, df{__fsub_rn(a.T, s), a.L});
-        a = RowAcc{s, 0.f};
-    }
-    // sigma for K products with this thread's x values (xs[K/CW*..] flattened) and |U| <= umax
-    template <int K> static __device__ __forceinline__ Sigma sigma(const XV *xs, float umax)
-    {
-        float m = 0.f;
-#pragma unroll
-        for (int q = 0; q < K; ++q) m = fmaxf(m, fmaxf(fabsf(xs[q].re.h), fabsf(xs[q].im.h)));
-        // bound on |partial sum| with a factor 2 for the lo words and rounding, doubled again
-        const float bound = 4.f * (float)K * umax * m;
-        if (!(bound > 0.f)) return 0x1p-100f;
-        int e;
         frexpf(bound, &e);                     // bound < 2^e
         return ldexpf(1.f, e > -100 ? e : -100);
+    }
+    // Column sums over chunks of at most K rows: the same accumulator, each
+    // chunk's (k, L) added to a running (k, L) for the segment.
+    template <int K> static __device__ __forceinline__ Sigma csigma(float xmax, float umax)
+    {
+        return rsigma<K>(xmax, umax);
+    }
+    using CRun = RComp;
+    static __device__ __forceinline__ CRun czero() { return RComp{0, 0.f}; }
+    static __device__ __forceinline__ double cto_double(CRun a, Sigma s) { return rto_double(a, s); }
+    static __device__ __forceinline__ float xabs(const XV &x) { return fmaxf(fabsf(x.re.h), fabsf(x.im.h)); }
+    static __device__ __forceinline__ void cfold(CRun &run, RowAcc &a, Sigma s)
+    {
+        run = radd(run, rdone(a, s));
+        a = rzero(s);
     }
     static __device__ __forceinline__ Comp shfl(Comp a, int m)
     {

@@ -36,7 +36,8 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
     constexpr int VS = 2 * RS;             // row components per stage
     constexpr int DUPS = 32 / VS;          // lanes holding the same stage component
     static_assert(RBT % RS == 0, "RS must divide RBT");
-    using Comp = typename P::Comp;
+    using RComp = typename P::RComp;
+    using CRun = typename P::CRun;
     using XV = typename P::XV;
     using Elem = typename P::Elem;
 
@@ -44,10 +45,10 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
     __shared__ __align__(8) uint64_t full[NS];
     __shared__ __align__(8) uint64_t empty[NS];
     __shared__ __align__(16) float4 xs_raw[NS][RBT];       // x_l rows of each stage, 16 bytes each
-    __shared__ Comp red[2][NW][V];
+    __shared__ RComp red[2][NW][V];
     __shared__ int abort_flag;
     __shared__ int issued, consumed;
-    __shared__ float xmax_sh[NW];
+    __shared__ float xmax_sh[NW], xrow_sh[NW];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -142,31 +143,40 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
             const int ngrp = (n + CW - 1) / CW;
             const int mine = tid < ngrp ? (ngrp - tid + CT - 1) / CT : 0;
             XV xc[MAXG][CW];
-            Comp car[MAXG][CW], cai[MAXG][CW];
+            CRun car[MAXG][CW], cai[MAXG][CW];
 #pragma unroll
             for (int g = 0; g < MAXG; ++g)
 #pragma unroll
                 for (int c = 0; c < CW; ++c) {
                     const int col = (tid + g * CT) * CW + c;
                     xc[g][c] = (col < n) ? P::loadx(S.xq, base_u + col) : P::zerox();
-                    car[g][c] = P::zero();
-                    cai[g][c] = P::zero();
+                    car[g][c] = P::czero();
+                    cai[g][c] = P::czero();
                 }
             const float um = S.umax ? S.umax[sg.l] : 0.f;
-            const typename P::Sigma sig = P::template sigma<MAXG * CW>(&xc[0][0], um);
-            // bound on |x_l| over the segment's rows, for the column sums
-            float xm = 0.f;
+            // bounds on |x_l| over the segment's rows (column sums) and on
+            // |x_{l+1}| over the row (row sums), each the same for the whole CTA
+            float xm = 0.f, xr = 0.f;
             if constexpr (P::kOffsetSums) {
                 for (int r = sg.i0 + tid; r < sg.i1; r += CT) xm = fmaxf(xm, P::xabs(P::loadx(S.xq, base_l + r)));
 #pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, off));
-                if (lane == 0) xmax_sh[warp] = xm;
+                for (int g = 0; g < MAXG; ++g)
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) xr = fmaxf(xr, P::xabs(xc[g][c]));
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) {
+                    xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, off));
+                    xr = fmaxf(xr, __shfl_xor_sync(0xffffffffu, xr, off));
+                }
+                if (lane == 0) { xmax_sh[warp] = xm; xrow_sh[warp] = xr; }
                 named_sync(1, CT);
                 xm = 0.f;
+                xr = 0.f;
 #pragma unroll
-                for (int w = 0; w < NW; ++w) xm = fmaxf(xm, xmax_sh[w]);
+                for (int w = 0; w < NW; ++w) { xm = fmaxf(xm, xmax_sh[w]); xr = fmaxf(xr, xrow_sh[w]); }
                 named_sync(1, CT);
             }
+            const typename P::Sigma sig = P::template rsigma<MAXG * CW>(xr, um);
             const typename P::Sigma csig = P::template csigma<RBT>(xm, um);
             typename P::RowAcc cpr[MAXG][CW], cpi[MAXG][CW];
 #pragma unroll
@@ -221,7 +231,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     if (lane == 0) mbar_arrive(&empty[s]);
                     ++q;
                     // warp transpose-reduce of the stage's 2*RS row components
-                    Comp v[VS];
+                    RComp v[VS];
 #pragma unroll
                     for (int rr = 0; rr < RS; ++rr) { v[2 * rr] = P::rdone(rre[rr], sig); v[2 * rr + 1] = P::rdone(rim[rr], sig); }
                     int idx = 0;
@@ -234,13 +244,13 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                             const bool up = (lane & off) != 0;
 #pragma unroll
                             for (int t = 0; t < half; ++t) {
-                                const Comp send = up ? v[t] : v[t + half];
-                                const Comp keep = up ? v[t + half] : v[t];
-                                v[t] = P::add_fast(keep, P::shfl(send, off));
+                                const RComp send = up ? v[t] : v[t + half];
+                                const RComp keep = up ? v[t + half] : v[t];
+                                v[t] = P::radd(keep, P::rshfl(send, off));
                             }
                             if (up) idx += half;
                         } else {
-                            v[0] = P::add_fast(v[0], P::shfl(v[0], off));
+                            v[0] = P::radd(v[0], P::rshfl(v[0], off));
                         }
                     }
                     if ((lane & (DUPS - 1)) == 0) red[parity][warp][st * VS + idx] = v[0];
@@ -258,11 +268,11 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                 if (warp == 0 && lane < V) {
                     const int i = rb + (lane >> 1);
                     if (i < sg.i1 && !*abort) {
-                        Comp sum = red[parity][0][lane];
+                        RComp sum = red[parity][0][lane];
 #pragma unroll
-                        for (int w = 1; w < NW; ++w) sum = P::add_fast(sum, red[parity][w][lane]);
+                        for (int w = 1; w < NW; ++w) sum = P::radd(sum, red[parity][w][lane]);
                         double *dst = reinterpret_cast<double *>(S.R + base_l + i) + (lane & 1);
-                        *dst = P::to_double(sum);
+                        *dst = P::rto_double(sum, sig);
                     }
                 }
                 parity ^= 1;
@@ -283,7 +293,8 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
 #pragma unroll
                     for (int c = 0; c < CW; ++c) {
                         const int col = (tid + g * CT) * CW + c;
-                        if (col < n) Pslot[col] = make_double2(P::to_double(car[g][c]), P::to_double(cai[g][c]));
+                        if (col < n)
+                            Pslot[col] = make_double2(P::cto_double(car[g][c], csig), P::cto_double(cai[g][c], csig));
                     }
             }
         }
