@@ -139,6 +139,9 @@ struct tdse_ctx {
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
     size_t prof_used = 0;               // events in use
+    long prof_products = 0;             // block products inside the traced launches
+    DevBuf gbar;                        // grid-barrier counter of the persistent stepping launches
+    int step_ok = -1;                   // whether the plan runs persistently (-1: not yet known)
     long launches = 0;
     ~tdse_ctx()
     {
@@ -552,7 +555,10 @@ static tdse_status launch_product(tdse_ctx *c, int slot, cudaStream_t s)
     else
         CUDA_TRY(tdse::launch_mv(c->prec, c->plan.cfg, c->plan.grid, sys, c->plan.segs.as<Seg>(),
                                  c->plan.cta_off.as<int>(), s));
-    if (traced) CUDA_TRY(cudaEventRecord(e1, s));
+    if (traced) {
+        CUDA_TRY(cudaEventRecord(e1, s));
+        c->prof_products += 1;
+    }
     c->launches += 1;
     return TDSE_OK;
 }
@@ -642,6 +648,66 @@ static tdse_status propagate_lanczos(tdse_ctx *ctx, double *c, int sps, double d
     return TDSE_OK;
 }
 
+// Whether every stage of a propagation runs in persistent launches: a
+// bulk-copy ring plan whose CTAs can all be resident at once, with FP64 or
+// float-float products.  (Measured: FP64 and float-float steps of an L2-resident
+// system 16% and 33% faster than one product and one update launch per stage;
+// FP32 products, shorter than the two grid barriers per stage, 14% slower.)
+static bool step_capable(tdse_ctx *ctx)
+{
+    if (ctx->step_ok < 0) {
+        ctx->step_ok = 0;
+        if (ctx->prec != TDSE_FP32 && ctx->plan.cfg.tma && ctx->plan.grid > 0 &&
+            tdse::mvt_step_fits(ctx->prec, ctx->plan.cfg, ctx->plan.grid) &&
+            ctx->gbar.ensure(sizeof(unsigned)) == cudaSuccess)
+            ctx->step_ok = 1;
+    }
+    return ctx->step_ok == 1;
+}
+
+// RK4 / Taylor stages of steps k0 .. k0+nsteps-1 in persistent launches (at
+// most 2^20 block products each, which keeps the grid-barrier counts far from
+// 2^32), the last `skip_last` passes left out.  `rec` (may be NULL) adds the
+// adjoint's checkpoint or stage-store writes.
+static tdse_status propagate_persistent(tdse_ctx *ctx, int sps, double dt, long nsteps, tdse_scheme scheme, int order,
+                                        int hold, cudaStream_t s, long k_first = 0, const tdse::StepArgs *rec = nullptr,
+                                        int skip_last = 0)
+{
+    const int per = scheme == TDSE_RK4 ? 4 : order;
+    const long max_steps = (1L << 20) / per;
+    for (long k0 = 0; k0 < nsteps; k0 += max_steps) {
+        const long ks = std::min(max_steps, nsteps - k0);
+        tdse::StepArgs A{};
+        if (rec) {
+            A = *rec;
+            if (A.store) A.store += (size_t)k0 * A.nst * ctx->N;     // indexed from the launch's first step
+        }
+        A.passes = (int)(ks * per) - (k0 + ks == nsteps ? skip_last : 0);
+        if (A.passes <= 0) break;
+        A.mode = scheme == TDSE_RK4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
+        A.order = order;
+        A.hold = hold;
+        A.sps = sps;
+        A.dt = dt;
+        A.k0 = k_first + k0;
+        A.gbar = ctx->gbar.as<unsigned>();
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ctx->prof_on) {
+            tdse_status st = prof_pair(ctx, &e0, &e1);
+            if (st != TDSE_OK) return st;
+            CUDA_TRY(cudaEventRecord(e0, s));
+        }
+        CUDA_TRY(tdse::launch_mvt_step(ctx->prec, ctx->plan.cfg, ctx->plan.grid, ctx->sys.as<SysDesc>(),
+                                       ctx->plan.segs.as<Seg>(), ctx->plan.cta_off.as<int>(), ctx->errw.as<int>(), A, s));
+        if (ctx->prof_on) {
+            CUDA_TRY(cudaEventRecord(e1, s));
+            ctx->prof_products += A.passes;
+        }
+        ctx->launches += 1;
+    }
+    return TDSE_OK;
+}
+
 static tdse_status propagate_impl(tdse_ctx *ctx, double *c, const double *field, int sps, double dt, long nsteps,
                                   tdse_scheme scheme, int order, int hold, cudaStream_t s)
 {
@@ -681,6 +747,7 @@ static tdse_status propagate_impl(tdse_ctx *ctx, double *c, const double *field,
     }
     CUDA_TRY(tdse::launch_prep(ctx->prec, ctx->plan.nblk, ctx->plan.blk.as<int2>(), ctx->sys.as<SysDesc>(), 0, s));
     ctx->launches += 1;
+    if (step_capable(ctx)) return propagate_persistent(ctx, sps, dt, nsteps, scheme, order, hold, s);
     tdse::EpiArgs a{};
     a.sps = sps;
     a.dt = dt;
@@ -982,9 +1049,10 @@ tdse_status tdse_profile_read(tdse_ctx *ctx, double *mv_ms, long *mv_launches, l
         ms += t;
     }
     if (mv_ms) *mv_ms = ms;
-    if (mv_launches) *mv_launches = (long)(ctx->prof_used / 2);
+    if (mv_launches) *mv_launches = ctx->prof_products;
     if (kernel_launches) *kernel_launches = ctx->launches;
     ctx->prof_used = 0;
+    ctx->prof_products = 0;
     ctx->launches = 0;
     return TDSE_OK;
 }
@@ -1201,7 +1269,16 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
     a.order = order;
     a.hold = taylor_hold;
     a.mode = rk4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
-    for (long k = 0; k < nsteps; ++k) {
+    const bool persistent = nsteps > 0 && step_capable(ctx);
+    if (persistent) {
+        tdse::StepArgs rec{};
+        rec.ckpt = ctx->ckpt.as<double2>();
+        rec.ckpt_every = K;
+        rec.k_end = nsteps;
+        st = propagate_persistent(ctx, sps, dt, nsteps, scheme, order, taylor_hold, s, 0, &rec);
+        if (st != TDSE_OK) return st;
+    }
+    for (long k = 0; k < nsteps && !persistent; ++k) {
         a.k = k;
         const bool cp = ((k + 1) % K == 0) && (k + 1) < nsteps;
         for (int q = rk4 ? 0 : 1; q <= (rk4 ? 3 : order); ++q) {
@@ -1231,7 +1308,14 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
         CUDA_TRY(cudaMemcpyAsync(cw, ckpt(j), vb, cudaMemcpyDeviceToDevice, s));
         CUDA_TRY(tdse::launch_prep(ctx->prec, nblk, ctx->plan.blk.as<int2>(), dfwd, 0, s));
         ctx->launches += 1;
-        for (long i = 0; i < ns; ++i) {
+        if (persistent) {
+            tdse::StepArgs rec{};
+            rec.store = store(0, 0);
+            rec.nst = nst;
+            st = propagate_persistent(ctx, sps, dt, ns, scheme, order, taylor_hold, s, k0, &rec, 1);
+            if (st != TDSE_OK) return st;
+        }
+        for (long i = 0; i < ns && !persistent; ++i) {
             a.k = k0 + i;
             const int qlast = rk4 ? 3 : order;
             for (int q = rk4 ? 0 : 1; q <= qlast; ++q) {

@@ -124,6 +124,13 @@ struct PolF64 {
         double2 v = reinterpret_cast<const double2 *>(xq)[a];
         return XV{v.x, v.y};
     }
+    // from global memory through L2 only (x may have been rewritten by another
+    // CTA of the same launch)
+    static __device__ __forceinline__ XV loadx_g(const void *xq, long long a)
+    {
+        double2 v = __ldcg(reinterpret_cast<const double2 *>(xq) + a);
+        return XV{v.x, v.y};
+    }
     static __device__ __forceinline__ XV zerox() { return XV{0.0, 0.0}; }
     static __device__ __forceinline__ Comp zero() { return 0.0; }
     static __device__ __forceinline__ void fmax_(Comp &re, Comp &im, Uv u, const XV &x)
@@ -191,6 +198,11 @@ struct PolF32 {
         float4 v = reinterpret_cast<const float4 *>(xq)[a];
         return XV{v.x, v.y};
     }
+    static __device__ __forceinline__ XV loadx_g(const void *xq, long long a)
+    {
+        float4 v = __ldcg(reinterpret_cast<const float4 *>(xq) + a);
+        return XV{v.x, v.y};
+    }
     static __device__ __forceinline__ XV zerox() { return XV{0.f, 0.f}; }
     static __device__ __forceinline__ Comp zero() { return 0.f; }
     static __device__ __forceinline__ void fmax_(Comp &re, Comp &im, Uv u, const XV &x)
@@ -255,6 +267,11 @@ struct PolDF32 {
     static __device__ __forceinline__ XV loadx(const void *xq, long long a)
     {
         float4 v = reinterpret_cast<const float4 *>(xq)[a];
+        return XV{df{v.x, v.y}, df{v.z, v.w}};
+    }
+    static __device__ __forceinline__ XV loadx_g(const void *xq, long long a)
+    {
+        float4 v = __ldcg(reinterpret_cast<const float4 *>(xq) + a);
         return XV{df{v.x, v.y}, df{v.z, v.w}};
     }
     static __device__ __forceinline__ XV zerox() { return XV{df{0.f, 0.f}, df{0.f, 0.f}}; }

@@ -31,12 +31,13 @@ __device__ __forceinline__ EpiPre epi_pre(const SysDesc &S, long long a)
 __device__ __forceinline__ double2 epi_dx(const SysDesc &S, long long a, const EpiPre &p)
 {
     double rr = 0.0, ri = 0.0, pr = 0.0, pi = 0.0;
+    // through L2 only: in a persistent launch other CTAs wrote these moments ago
     if (p.m < S.lmax) {
-        const double2 r = S.R[a];
+        const double2 r = __ldcg(S.R + a);
         rr = r.x; ri = r.y;
     }
     for (int s = p.b0; s < p.b1; ++s) {
-        const double2 q = S.P[(long long)s * S.n + p.i];
+        const double2 q = __ldcg(S.P + (long long)s * S.n + p.i);
         pr += q.x; pi += q.y;
     }
     if (S.gauge == 0) return make_double2(rr + pr, ri + pi);

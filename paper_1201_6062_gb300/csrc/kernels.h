@@ -44,6 +44,34 @@ bool mvt_rs_valid(int prec, const MvCfg &cfg, int rs, int ld);
 cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys, const Seg *segs,
                        const int *cta_off, int *err, cudaStream_t stream);
 
+// Persistent stepping of one system (mvt.cuh, STEP instances): `passes` block
+// products in one cooperative launch, each followed by a grid barrier, the
+// stage update (RK4 stage or Taylor term, App. B) of a contiguous slice of
+// amplitudes per CTA, and a second grid barrier; the producer warp keeps
+// streaming the next product's dipole rows through both barriers.
+struct StepArgs {
+    int passes;            // block products (stages of all steps) in this launch
+    int mode;              // EPI_RK4 or EPI_TAYLOR
+    int order, hold, sps;  // Taylor order and hold, samples per step
+    double dt;
+    long long k0;          // step index of the first pass (a pass is one stage)
+    unsigned *gbar;        // grid-barrier arrival counter, zero at launch
+    // Adjoint forward pass: after step k, if (k+1) % ckpt_every == 0 and
+    // k+1 < k_end, c is also written to ckpt[(k+1)/ckpt_every] (NULL: none).
+    double2 *ckpt;
+    long long ckpt_every, k_end;
+    // Adjoint recompute: the input of stage q of step k0+i is also written to
+    // store[i*nst + q] (RK4: q = stage+1; Taylor: q = term), the state after
+    // the step to store[(i+1)*nst] (NULL: none).
+    double2 *store;
+    int nst;
+};
+// Whether the plan's CTAs can all be resident at once (required: the CTAs
+// wait for one another at the grid barriers).
+bool mvt_step_fits(int prec, const MvCfg &cfg, int grid);
+cudaError_t launch_mvt_step(int prec, const MvCfg &cfg, int grid, const SysDesc *sys, const Seg *segs,
+                            const int *cta_off, int *err, const StepArgs &a, cudaStream_t stream);
+
 // Block mat-vec over a segment list: R = U_l x_{l+1} rows, P = column partials.
 cudaError_t launch_mv(int prec, const MvCfg &cfg, int grid, const SysDesc *sys,
                       const Seg *segs, const int *cta_off, cudaStream_t stream);

@@ -4,12 +4,12 @@
 
 namespace tdse {
 
-static const void *mvt_fn_prec(int prec, int idx, int rs)
+static const void *mvt_fn_prec(int prec, int idx, int rs, bool step = false)
 {
     switch (prec) {
-    case 0: return mvt_fn_f64(idx, rs);
-    case 1: return mvt_fn_f32(idx, rs);
-    case 2: return mvt_fn_df32(idx, rs);
+    case 0: return step ? mvt_fn_f64_step(idx, rs) : mvt_fn_f64_product(idx, rs);
+    case 1: return step ? mvt_fn_f32_step(idx, rs) : mvt_fn_f32_product(idx, rs);
+    case 2: return step ? mvt_fn_df32_step(idx, rs) : mvt_fn_df32_product(idx, rs);
     }
     return nullptr;
 }
@@ -84,8 +84,59 @@ cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys,
     const int smem = cfg.per_sm > 1 ? NS * stage : NS * STAGE_MAX;
     const cudaError_t e = ensure_dyn_smem(fn, NS * STAGE_MAX);
     if (e != cudaSuccess) return e;
-    void *args[] = {(void *)&sys, (void *)&segs, (void *)&cta_off, (void *)&err, (void *)&stage};
+    StepArgs none{};
+    none.passes = 1;
+    void *args[] = {(void *)&sys, (void *)&segs, (void *)&cta_off, (void *)&err, (void *)&stage, (void *)&none};
     return launch_pdl(fn, dim3(grid), dim3(cfg.BT), (size_t)smem, stream, args);
+}
+
+// Dynamic shared memory of a launch: one CTA per SM requests the whole ring
+// so that no two of its CTAs share an SM.
+static int launch_smem(int prec, const MvCfg &cfg)
+{
+    return cfg.per_sm > 1 ? NS * stage_bytes(prec, cfg) : NS * STAGE_MAX;
+}
+
+bool mvt_step_fits(int prec, const MvCfg &cfg, int grid)
+{
+    const void *fn = mvt_fn_prec(prec, cfg.idx, cfg.RS, true);
+    if (!fn || cfg.ld <= 0 || grid <= 0) return false;
+    if (stage_bytes(prec, cfg) > STAGE_MAX) return false;
+    if (ensure_dyn_smem(fn, NS * STAGE_MAX) != cudaSuccess) return false;
+    int dev = 0, sms = 0, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, cfg.BT, (size_t)launch_smem(prec, cfg)) != cudaSuccess)
+        return false;
+    return (long long)nb * sms >= grid;
+}
+
+cudaError_t launch_mvt_step(int prec, const MvCfg &cfg, int grid, const SysDesc *sys, const Seg *segs,
+                            const int *cta_off, int *err, const StepArgs &a, cudaStream_t stream)
+{
+    const void *fn = mvt_fn_prec(prec, cfg.idx, cfg.RS, true);
+    if (!fn || cfg.ld <= 0 || grid <= 0) return cudaErrorInvalidValue;
+    int stage = stage_bytes(prec, cfg);
+    if (stage > STAGE_MAX) return cudaErrorInvalidValue;
+    const cudaError_t e = ensure_dyn_smem(fn, NS * STAGE_MAX);
+    if (e != cudaSuccess) return e;
+    // zero the grid-barrier counter, then one cooperative launch: the CTAs
+    // wait for one another, so all of them must be resident together
+    const cudaError_t z = cudaMemsetAsync(a.gbar, 0, sizeof(unsigned), stream);
+    if (z != cudaSuccess) return z;
+    StepArgs sa = a;
+    void *args[] = {(void *)&sys, (void *)&segs, (void *)&cta_off, (void *)&err, (void *)&stage, (void *)&sa};
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(cfg.BT);
+    lc.dynamicSmemBytes = (size_t)launch_smem(prec, cfg);
+    lc.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelExC(&lc, fn, args);
 }
 
 }  // namespace tdse

@@ -12,8 +12,21 @@
 // consumers' register budget, which the per-thread loads of mv.cu cannot.
 // All waits are bounded (sync.cuh); a timeout raises kErrTimeout in *err and
 // the CTA drains and exits.
+//
+// STEP instances run all stages of a propagation of one system in one
+// cooperative launch (StepArgs in kernels.h): after each product a grid
+// barrier (every row sum and column partial written), the stage update of a
+// contiguous slice of amplitudes per CTA (epi.cuh), and a second grid barrier
+// (every next-stage input written).  The producer warp streams the next
+// product's dipole rows through both barriers and holds back only the copies
+// of the stage inputs x, which it issues once the second barrier is passed.
+// Data that another CTA rewrote within the launch is read through L2 only
+// (__ldcg), and the bulk copies of x follow a fence.proxy.async.  The grid
+// barriers are bounded waits too; a CTA that gives up raises kErrTimeout at
+// once, so that the others give up at their next barrier.
 #pragma once
 #include "kernels.h"
+#include "epi.cuh"
 #include "sync.cuh"
 
 namespace tdse {
@@ -25,10 +38,49 @@ constexpr int STAGE_MAX = 65536;       // bytes of dipole rows per stage, at mos
                                        // each stage to RS rows of the longest row stride it serves)
 constexpr uint64_t WAIT_NS = 2000000000ull;   // 2 s bound on any single wait
 
-template <class P, int CT, int MAXG, int RS>
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier of the consumer threads of all CTAs (STEP instances): every
+// thread's writes are made visible device-wide, one arrival per CTA, thread 0
+// waits (bounded) until `target` CTAs have arrived.  Returns false, the same
+// in every consumer thread, when this CTA or another one has given up.
+__device__ __forceinline__ bool grid_sync(unsigned *ctr, unsigned target, volatile int *abort, int *err,
+                                          volatile int *go, int tid, int nthreads)
+{
+    __threadfence();
+    named_sync(1, nthreads);
+    if (tid == 0) {
+        int ok = !*abort;
+        if (ok) {
+            atomicAdd(ctr, 1u);
+            volatile int *gerr = err;
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_acquire_gpu(ctr) < target) {
+                if ((*gerr & kErrTimeout) != 0 || globaltimer_ns() - t0 > WAIT_NS) {
+                    *abort = 1;
+                    atomicOr(err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        } else {
+            atomicOr(err, kErrTimeout);
+        }
+        *go = ok;
+    }
+    named_sync(1, nthreads);
+    return *go != 0;
+}
+
+template <class P, int CT, int MAXG, int RS, bool STEP>
 __global__ void __launch_bounds__(CT + 32, 1)
 mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const int *__restrict__ cta_off,
-           int *__restrict__ err, int stage)
+           int *__restrict__ err, int stage, const __grid_constant__ StepArgs A)
 {
     constexpr int CW = P::CW;
     constexpr int NW = CT / 32;
@@ -50,6 +102,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
     __shared__ int abort_flag;
     __shared__ int issued, consumed;
     __shared__ float xmax_sh[NW], xrow_sh[NW];
+    __shared__ int xready, go_flag;       // STEP: passes whose stage inputs are written; barrier verdict
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -61,10 +114,13 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
         abort_flag = 0;
         issued = 0;
         consumed = 0;
+        xready = 0;
+        go_flag = 0;
         fence_mbar_init();
     }
     __syncthreads();
     const int s0 = cta_off[blockIdx.x], s1 = cta_off[blockIdx.x + 1];
+    const int npass = STEP ? A.passes : 1;
     const uint64_t pol = l2_evict_first_policy();
     const uint64_t pol_x = l2_evict_last_policy();
     // The dipole rows and the plan never change between launches: the producer
@@ -98,41 +154,89 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
         // ---------------------------------------------------- producer warp
         int q = 0;
         bool ok = true;
-        for (int si = s0; si < s1 && ok; ++si) {
-            const Seg sg = segs[si];
-            const SysDesc &S = sys[sg.sys];
-            const long long ld = S.ld;
-            const Elem *Ub = reinterpret_cast<const Elem *>(S.U) + (long long)sg.l * S.bstride;
-            const long long base_l = (long long)sg.l * S.n;
-            for (int r = sg.i0; r < sg.i1; r += RS) {
-                const int nr = min(RS, sg.i1 - r);
-                const int s = q % NS;
-                const int k = q / NS;
-                if (k > 0) {
-                    bool w = true;
-                    if (lane == 0) w = mbar_wait_bounded(&empty[s], (uint32_t)((k - 1) & 1), abort, WAIT_NS);
-                    w = __shfl_sync(0xffffffffu, w, 0);
-                    if (!w) { ok = false; break; }
+        // STEP: x copies of stages of a pass whose inputs are not written yet
+        // (lane 0 only): issued once the consumers report the pass ready
+        int pend_n = 0, pend_pass = 0;
+        int pend_s[NS];
+        const char *pend_src[NS];
+        uint32_t pend_b[NS];
+        auto flush = [&]() -> bool {
+            bool good = true;
+            if (lane == 0 && pend_n > 0) {
+                volatile int *xr = &xready;
+                const uint64_t t0 = globaltimer_ns();
+                while (*xr < pend_pass) {
+                    if (*abort || globaltimer_ns() - t0 > WAIT_NS) { *abort = 1; good = false; break; }
                 }
-                if (lane == 0) {
-                    const uint32_t xbytes = (uint32_t)(nr * 16);
-                    if (q >= npre) {           // (stages q < npre: dipole rows already in flight)
-                        const uint32_t bytes = (uint32_t)(nr * ld * (long long)sizeof(Elem));
-                        mbar_arrive_expect_tx(&full[s], bytes + xbytes);
-                        bulk_g2s(ring + (size_t)s * stage, Ub + (long long)r * ld, bytes, &full[s], pol);
+                __threadfence_block();
+                if (good) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    for (int j = 0; j < pend_n; ++j)
+                        bulk_g2s(&xs_raw[pend_s[j]][0], pend_src[j], pend_b[j], &full[pend_s[j]], pol_x);
+                }
+                pend_n = 0;
+            }
+            return __shfl_sync(0xffffffffu, good, 0);
+        };
+        for (int pass = 0; pass < npass && ok; ++pass) {
+            for (int si = s0; si < s1 && ok; ++si) {
+                const Seg sg = segs[si];
+                const SysDesc &S = sys[sg.sys];
+                const long long ld = S.ld;
+                const Elem *Ub = reinterpret_cast<const Elem *>(S.U) + (long long)sg.l * S.bstride;
+                const long long base_l = (long long)sg.l * S.n;
+                for (int r = sg.i0; r < sg.i1; r += RS) {
+                    const int nr = min(RS, sg.i1 - r);
+                    const int s = q % NS;
+                    const int k = q / NS;
+                    if (STEP) {
+                        // held-back copies all belong to one pass: issue those of an
+                        // earlier pass before holding back any of this one
+                        const int older = __shfl_sync(0xffffffffu, (pend_n > 0 && pend_pass != pass) ? 1 : 0, 0);
+                        if (older && !flush()) { ok = false; break; }
                     }
-                    bulk_g2s(&xs_raw[s][0], reinterpret_cast<const char *>(S.xq) + (base_l + r) * 16, xbytes, &full[s],
-                             pol_x);
+                    if (k > 0) {
+                        // the slot is freed only after its stage was consumed, which
+                        // needs any held-back x copy of an earlier slot first
+                        if (STEP && !flush()) { ok = false; break; }
+                        bool w = true;
+                        if (lane == 0) w = mbar_wait_bounded(&empty[s], (uint32_t)((k - 1) & 1), abort, WAIT_NS);
+                        w = __shfl_sync(0xffffffffu, w, 0);
+                        if (!w) { ok = false; break; }
+                    }
+                    if (lane == 0) {
+                        const uint32_t xbytes = (uint32_t)(nr * 16);
+                        if (q >= npre) {           // (stages q < npre: dipole rows already in flight)
+                            const uint32_t bytes = (uint32_t)(nr * ld * (long long)sizeof(Elem));
+                            mbar_arrive_expect_tx(&full[s], bytes + xbytes);
+                            bulk_g2s(ring + (size_t)s * stage, Ub + (long long)r * ld, bytes, &full[s], pol);
+                        }
+                        const char *xsrc = reinterpret_cast<const char *>(S.xq) + (base_l + r) * 16;
+                        const bool held = STEP && pass > 0 && *(volatile int *)&xready < pass;
+                        if (STEP && pass > 0) __threadfence_block();
+                        if (held) {
+                            pend_s[pend_n] = s;
+                            pend_src[pend_n] = xsrc;
+                            pend_b[pend_n] = xbytes;
+                            pend_pass = pass;
+                            ++pend_n;
+                        } else {
+                            if (STEP && pass > 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+                            bulk_g2s(&xs_raw[s][0], xsrc, xbytes, &full[s], pol_x);
+                        }
+                    }
+                    __syncwarp();
+                    ++q;
                 }
-                __syncwarp();
-                ++q;
             }
         }
+        if (STEP && !flush()) ok = false;
         if (lane == 0) issued = q;
     } else {
         // ------------------------------------------------- consumer warps
         int q = 0;
         int parity = 0;
+        for (int pass = 0; pass < npass; ++pass) {
         for (int si = s0; si < s1; ++si) {
             const Seg sg = segs[si];
             const SysDesc &S = sys[sg.sys];
@@ -150,7 +254,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
 #pragma unroll
                 for (int c = 0; c < CW; ++c) {
                     const int col = (tid + g * CT) * CW + c;
-                    xc[g][c] = (col < n) ? P::loadx(S.xq, base_u + col) : P::zerox();
+                    xc[g][c] = (col < n) ? P::loadx_g(S.xq, base_u + col) : P::zerox();
                     car[g][c] = P::czero();
                     cai[g][c] = P::czero();
                 }
@@ -159,7 +263,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
             // |x_{l+1}| over the row (row sums), each the same for the whole CTA
             float xm = 0.f, xr = 0.f;
             if constexpr (P::kOffsetSums) {
-                for (int r = sg.i0 + tid; r < sg.i1; r += CT) xm = fmaxf(xm, P::xabs(P::loadx(S.xq, base_l + r)));
+                for (int r = sg.i0 + tid; r < sg.i1; r += CT) xm = fmaxf(xm, P::xabs(P::loadx_g(S.xq, base_l + r)));
 #pragma unroll
                 for (int g = 0; g < MAXG; ++g)
 #pragma unroll
@@ -299,6 +403,45 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                     }
             }
         }
+        if constexpr (STEP) {
+            // every row sum and column partial of this pass is written
+            if (!grid_sync(A.gbar, (unsigned)(2 * pass + 1) * gridDim.x, abort, err, &go_flag, tid, CT)) break;
+            // the stage update of this CTA's slice of amplitudes
+            const SysDesc &S0 = sys[0];
+            const int per = A.mode == EPI_RK4 ? 4 : A.order;
+            EpiArgs e{};
+            e.mode = A.mode;
+            e.stage = A.mode == EPI_RK4 ? pass % per : pass % per + 1;
+            e.order = A.order;
+            e.hold = A.hold;
+            e.sps = A.sps;
+            e.dt = A.dt;
+            e.k = A.k0 + pass / per;
+            const long long N = S0.N;
+            const int qlast = A.mode == EPI_RK4 ? 3 : A.order;
+            if (A.ckpt && e.stage == qlast && (e.k + 1) % A.ckpt_every == 0 && e.k + 1 < A.k_end)
+                e.st_c = A.ckpt + (size_t)((e.k + 1) / A.ckpt_every) * N;
+            if (A.store) {
+                const long long i = pass / per;
+                if (e.stage < qlast)
+                    e.st_x = A.store + (size_t)(i * A.nst + (A.mode == EPI_RK4 ? e.stage + 1 : e.stage)) * N;
+                else
+                    e.st_c = A.store + (size_t)((i + 1) * A.nst) * N;
+            }
+            const long long a1 = N * (blockIdx.x + 1) / gridDim.x;
+#pragma unroll 1
+            for (long long a = N * blockIdx.x / gridDim.x + tid; a < a1; a += CT) {
+                const EpiPre pre = epi_pre(S0, a);
+                epi_amp<P>(S0, a, e, pre);
+            }
+            // every input of the next pass is written
+            if (!grid_sync(A.gbar, (unsigned)(2 * pass + 2) * gridDim.x, abort, err, &go_flag, tid, CT)) break;
+            if (tid == 0) {
+                __threadfence_block();
+                *(volatile int *)&xready = pass + 1;
+            }
+        }
+        }
         if (tid == 0) consumed = q;
     }
     __syncthreads();
@@ -317,38 +460,41 @@ struct TCfg { int CT, MAXG; };
 constexpr TCfg kTCfg[] = {{128, 1}, {128, 2}, {192, 2}, {256, 2}, {192, 3}, {256, 3}, {256, 4}, {512, 4}};
 constexpr int kNumTCfg = sizeof(kTCfg) / sizeof(kTCfg[0]);
 
-template <class P, int CT, int MAXG>
+template <class P, int CT, int MAXG, bool STEP>
 inline const void *mvt_fn_rs(int rs)
 {
     switch (rs) {
-    case 1: return (const void *)mvt_kernel<P, CT, MAXG, 1>;
-    case 2: return (const void *)mvt_kernel<P, CT, MAXG, 2>;
-    case 4: return (const void *)mvt_kernel<P, CT, MAXG, 4>;
-    case 8: return (const void *)mvt_kernel<P, CT, MAXG, 8>;
+    case 1: return (const void *)mvt_kernel<P, CT, MAXG, 1, STEP>;
+    case 2: return (const void *)mvt_kernel<P, CT, MAXG, 2, STEP>;
+    case 4: return (const void *)mvt_kernel<P, CT, MAXG, 4, STEP>;
+    case 8: return (const void *)mvt_kernel<P, CT, MAXG, 8, STEP>;
     }
     return nullptr;
 }
 
-template <class P>
+template <class P, bool STEP>
 inline const void *mvt_fn(int idx, int rs)
 {
     switch (idx) {
-    case 0: return mvt_fn_rs<P, 128, 1>(rs);
-    case 1: return mvt_fn_rs<P, 128, 2>(rs);
-    case 2: return mvt_fn_rs<P, 192, 2>(rs);
-    case 3: return mvt_fn_rs<P, 256, 2>(rs);
-    case 4: return mvt_fn_rs<P, 192, 3>(rs);
-    case 5: return mvt_fn_rs<P, 256, 3>(rs);
-    case 6: return mvt_fn_rs<P, 256, 4>(rs);
-    case 7: return rs <= 2 ? mvt_fn_rs<P, 512, 4>(rs) : nullptr;
+    case 0: return mvt_fn_rs<P, 128, 1, STEP>(rs);
+    case 1: return mvt_fn_rs<P, 128, 2, STEP>(rs);
+    case 2: return mvt_fn_rs<P, 192, 2, STEP>(rs);
+    case 3: return mvt_fn_rs<P, 256, 2, STEP>(rs);
+    case 4: return mvt_fn_rs<P, 192, 3, STEP>(rs);
+    case 5: return mvt_fn_rs<P, 256, 3, STEP>(rs);
+    case 6: return mvt_fn_rs<P, 256, 4, STEP>(rs);
+    case 7: return rs <= 2 ? mvt_fn_rs<P, 512, 4, STEP>(rs) : nullptr;
     }
     return nullptr;
 }
 
-// One translation unit per precision instantiates its kernels (mvt_f64.cu,
-// mvt_f32.cu, mvt_df32.cu), so they compile in parallel.
-const void *mvt_fn_f64(int idx, int rs);
-const void *mvt_fn_f32(int idx, int rs);
-const void *mvt_fn_df32(int idx, int rs);
+// One translation unit per precision and kind instantiates the kernels
+// (mvt_f64.cu, mvt_f64_step.cu, ...), so they compile in parallel.
+const void *mvt_fn_f64_product(int idx, int rs);
+const void *mvt_fn_f32_product(int idx, int rs);
+const void *mvt_fn_df32_product(int idx, int rs);
+const void *mvt_fn_f64_step(int idx, int rs);
+const void *mvt_fn_f32_step(int idx, int rs);
+const void *mvt_fn_df32_step(int idx, int rs);
 
 }  // namespace tdse

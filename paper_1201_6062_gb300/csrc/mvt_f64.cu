@@ -1,7 +1,7 @@
-// Ring-fed block mat-vec kernels with FP64 products (every thread layout
-// and ring depth).
+// Ring-fed block mat-vec kernels with FP64 products, one product per launch
+// (every thread layout and ring depth).
 #include "mvt.cuh"
 
 namespace tdse {
-const void *mvt_fn_f64(int idx, int rs) { return mvt_fn<PolF64>(idx, rs); }
+const void *mvt_fn_f64_product(int idx, int rs) { return mvt_fn<PolF64, false>(idx, rs); }
 }  // namespace tdse
