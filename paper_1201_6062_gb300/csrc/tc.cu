@@ -142,50 +142,69 @@ __device__ __forceinline__ void split_bf16(df v, __nv_bfloat16 *h, __nv_bfloat16
     *l = __float2bfloat16_rn(__fadd_rn(__fsub_rn(v.h, __bfloat162float(hb)), v.l));
 }
 
-// The state values one (pulse, amplitude) update reads: the stage input,
-// c (RK4 stages after the first) and the accumulator.  Loaded for several
-// pulses before any of their updates stores, so the loads overlap instead of
-// each waiting behind the previous update's stores.
-struct TcIn { float4 x, c, acc; };
+// The state values one (pulse, amplitude) update reads.  RK4: c (float-float)
+// and, after the first stage, one float4 with the FP32 accumulator
+// sum_j b_j k_j so far and the previous stage's derivative k_{s-1}, from which
+// the stage input c + a_s dt k_{s-1} is rebuilt in float-float (the FP32
+// rounding of k_{s-1}, about 2^-24 |a_s dt k_{s-1}|, stays far below the
+// bf16x3 products' error).  That is 208 bytes of state per (pulse, amplitude)
+// and step instead of 304 with a float-float stage input and accumulator.
+// Taylor: the previous term (float-float) and the partial sum.  Loaded for
+// several pulses before any of their updates stores, so the loads overlap
+// instead of each waiting behind the previous update's stores.
+template <bool RK4> struct TcIn;
+template <> struct TcIn<true> { float4 c, acc; };
+template <> struct TcIn<false> { float4 x, acc; };
 
-__device__ __forceinline__ void tc_load(const TcArgs &A, long long q, bool rk4, bool from_c, TcIn &in)
+template <bool RK4>
+__device__ __forceinline__ void tc_load(const TcArgs &A, long long q, bool from_c, TcIn<RK4> &in)
 {
-    in.x = from_c ? A.c[q] : A.x[q];
-    if (rk4 && !from_c) in.c = A.c[q];
-    if (rk4 ? A.stage >= 1 : A.stage > 1) in.acc = A.acc[q];
+    if constexpr (RK4) {
+        in.c = A.c[q];
+        if (A.stage >= 1) in.acc = A.acc[q];
+    } else {
+        in.x = from_c ? A.c[q] : A.x[q];
+        if (A.stage > 1) in.acc = A.acc[q];
+    }
 }
 
 __device__ __forceinline__ dfc as_dfc(float4 v) { return dfc{df{v.x, v.y}, df{v.z, v.w}}; }
 
 // One (pulse b, amplitude a) with D x = (dr, di): RK4 stage / Taylor term.
+template <bool RK4>
 __device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, df e, df f, float dr, float di,
-                                          const TcIn &in)
+                                          const TcIn<RK4> &in)
 {
     const long long q = (long long)b * A.N + a;
-    const bool rk4 = A.mode == 2;
-    const bool from_c = rk4 ? (A.stage == 0) : (A.stage == 1);
-    const dfc xin = as_dfc(in.x);
+    dfc xin;
+    if constexpr (RK4) {
+        const dfc c = as_dfc(in.c);
+        if (A.stage == 0) {
+            xin = c;
+        } else {
+            const df s = A.stage == 3 ? A.full_dt : A.half_dt;       // a_s dt
+            xin = dfc{df_add(c.re, df_mulf(s, in.acc.z)), df_add(c.im, df_mulf(s, in.acc.w))};
+        }
+    } else {
+        xin = as_dfc(in.x);
+    }
     if (A.gauge) { const float t = dr; dr = -di; di = t; }
     // H x = E x + f D x ;  k = -i H x = (Im, -Re)
     const df hr = df_add(df_mul(e, xin.re), df_mulf(f, dr));
     const df hi = df_add(df_mul(e, xin.im), df_mulf(f, di));
     const dfc k{hi, df_neg(hr)};
     dfc out;
-    if (rk4) {
-        const dfc c = from_c ? xin : as_dfc(in.c);
+    if constexpr (RK4) {
+        const dfc c = as_dfc(in.c);
+        const float kr = __fadd_rn(k.re.h, k.re.l), ki = __fadd_rn(k.im.h, k.im.l);
         if (A.stage == 0) {
-            st_dfc(A.acc + q, k);
+            A.acc[q] = make_float4(kr, ki, kr, ki);
             out = dfc_axpy(c, A.half_dt, k);
-            st_dfc(A.x + q, out);
         } else if (A.stage < 3) {
-            const dfc ac = as_dfc(in.acc);
-            const df two{2.f, 0.f};
-            st_dfc(A.acc + q, dfc{df_add(ac.re, df_mul(two, k.re)), df_add(ac.im, df_mul(two, k.im))});
+            A.acc[q] = make_float4(__fmaf_rn(2.f, kr, in.acc.x), __fmaf_rn(2.f, ki, in.acc.y), kr, ki);
             out = dfc_axpy(c, A.stage == 1 ? A.half_dt : A.full_dt, k);
-            st_dfc(A.x + q, out);
         } else {
-            const dfc ac = as_dfc(in.acc);
-            const dfc s{df_add(ac.re, k.re), df_add(ac.im, k.im)};
+            const dfc s{df_add(df{in.acc.x, 0.f}, k.re), df_add(df{in.acc.y, 0.f}, k.im)};
             out = dfc_axpy(c, A.sixth_dt, s);
             st_dfc(A.c + q, out);
         }
@@ -216,9 +235,12 @@ __device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, d
 constexpr int EPI_WARPS = 16;                       // a multiple of 4: EPI_WARPS / 4 per TMEM lane quarter
 constexpr int EPI_CPW = (TBN / 16) / (EPI_WARPS / 4); // 16-column accumulator chunks per epilogue warp
 static_assert(EPI_CPW * (EPI_WARPS / 4) * 16 == TBN, "epilogue warps must split the tile's columns evenly");
-constexpr int TC_LOAD_GROUP = 2;                   // pulses whose state loads are issued together
+constexpr int TC_LOAD_GROUP = 4;                   // pulses whose state loads are issued together
+                                                   // (2 and 8: 2% slower / spills; 64-pulse
+                                                   // tiles beat 32-pulse ones, 0.49 vs 0.57 ms a step)
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA issuer, epilogue
 
+template <bool RK4>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUtensorMap tmUl,
           const __grid_constant__ CUtensorMap tmTh, const __grid_constant__ CUtensorMap tmTl,
@@ -359,17 +381,16 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
                     for (int q = 0; q < 16; ++q) v[q] = 0.f;
                 }
                 if (valid_row) {
-                    const bool rk4 = A.mode == 2;
-                    const bool from_c = rk4 ? (A.stage == 0) : (A.stage == 1);
+                    const bool from_c = RK4 ? (A.stage == 0) : (A.stage == 1);
 #pragma unroll
                     for (int g = 0; g < 8; g += TC_LOAD_GROUP) {
-                        TcIn in[TC_LOAD_GROUP];
+                        TcIn<RK4> in[TC_LOAD_GROUP];
                         float2 fv[TC_LOAD_GROUP];
 #pragma unroll
                         for (int u = 0; u < TC_LOAD_GROUP; ++u) {
                             const int b = c0 / 2 + chunk * 8 + g + u;      // pulse
                             if (b < A.B) {
-                                tc_load(A, (long long)b * A.N + a, rk4, from_c, in[u]);
+                                tc_load<RK4>(A, (long long)b * A.N + a, from_c, in[u]);
                                 fv[u] = __ldg(A.fdf + b);
                             }
                         }
@@ -377,7 +398,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
                         for (int u = 0; u < TC_LOAD_GROUP; ++u) {
                             const int jj = g + u;
                             const int b = c0 / 2 + chunk * 8 + jj;
-                            if (b < A.B) tc_update(A, b, a, e, df{fv[u].x, fv[u].y}, v[2 * jj], v[2 * jj + 1], in[u]);
+                            if (b < A.B) tc_update<RK4>(A, b, a, e, df{fv[u].x, fv[u].y}, v[2 * jj], v[2 * jj + 1], in[u]);
                         }
                     }
                 }
@@ -465,7 +486,9 @@ __global__ void tc_out_kernel(const float4 *__restrict__ cdf, double2 *__restric
 
 cudaError_t launch_tc(const TcMaps &m, const TcArgs &A, cudaStream_t stream)
 {
-    const cudaError_t ea = ensure_dyn_smem((const void *)tc_kernel, TC_SMEM);
+    const bool rk4 = A.mode == EPI_RK4;
+    const void *fn = rk4 ? (const void *)tc_kernel<true> : (const void *)tc_kernel<false>;
+    const cudaError_t ea = ensure_dyn_smem(fn, TC_SMEM);
     if (ea != cudaSuccess) return ea;
     int sms = 0;
     {
@@ -476,7 +499,8 @@ cudaError_t launch_tc(const TcMaps &m, const TcArgs &A, cudaStream_t stream)
     }
     const int ntiles = ((A.n + TBM - 1) / TBM) * ((2 * A.B + TBN - 1) / TBN) * (A.lmax + 1);
     const int grid = ntiles < sms ? ntiles : sms;
-    tc_kernel<<<grid, TC_THREADS, TC_SMEM, stream>>>(m.Uh, m.Ul, m.Th, m.Tl, m.Xh, m.Xl, A);
+    if (rk4) tc_kernel<true><<<grid, TC_THREADS, TC_SMEM, stream>>>(m.Uh, m.Ul, m.Th, m.Tl, m.Xh, m.Xl, A);
+    else tc_kernel<false><<<grid, TC_THREADS, TC_SMEM, stream>>>(m.Uh, m.Ul, m.Th, m.Tl, m.Xh, m.Xl, A);
     return cudaGetLastError();
 }
 

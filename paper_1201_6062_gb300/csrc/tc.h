@@ -29,7 +29,8 @@ struct TcArgs {
     const float2 *Edf;      // energies as float-float [N]
     const double *field;    // [B][S]
     const float2 *fdf;      // this stage's field value per pulse, float-float [B]
-    float4 *c, *x, *acc;    // float-float complex states [B][N]
+    float4 *c, *x, *acc;    // states [B][N]: c float-float; RK4: acc = (FP32 accumulator, FP32 k of the
+                            // previous stage), x unused; Taylor: x previous term, acc partial sum (float-float)
     __nv_bfloat16 *xo_h, *xo_l;   // output planes [2B][plane]
     int *err;
 };

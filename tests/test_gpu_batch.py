@@ -140,6 +140,24 @@ def test_bf16x3_batched_rk4_matches_oracle(tdse_lib, lmax, n, B, nsteps):
         assert rel(got[b], ref) < 1e-5, b
 
 
+def test_bf16x3_batched_long_window_stays_within_tolerance(tdse_lib):
+    """600 RK4 steps of a pulse sweep on the ground state: the FP32 accumulator
+    and stage derivative kept between stages add no drift beyond the bf16x3
+    products' tolerance."""
+    lmax, n, B, dt, nsteps = 3, 500, 4, 0.02, 600
+    E, U, F, _ = sweep(lmax, n, B, nsteps, 2)
+    C0 = np.stack([inputs.ground_state(lmax, n)] * B)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "bf16x3")
+    c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(c, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps, samples_per_step=2)
+    H.sync()
+    got = c.cpu().numpy().reshape(B, -1)
+    for b in range(B):
+        ref, _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, nsteps, samples_per_step=2)
+        assert rel(got[b], ref) < 1e-5, b
+        assert abs(np.vdot(got[b], got[b]).real - 1.0) < 1e-6
+
+
 @pytest.mark.parametrize("K,hold,sps", [(6, 0, 1), (5, 1, 2)])
 def test_bf16x3_batched_taylor_matches_oracle(tdse_lib, K, hold, sps):
     lmax, n, B, dt, nsteps = 3, 300, 9, 0.02, 12
