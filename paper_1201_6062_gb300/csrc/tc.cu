@@ -171,8 +171,11 @@ __device__ __forceinline__ void tc_load(const TcArgs &A, long long q, bool from_
 __device__ __forceinline__ dfc as_dfc(float4 v) { return dfc{df{v.x, v.y}, df{v.z, v.w}}; }
 
 // One (pulse b, amplitude a) with D x = (dr, di): RK4 stage / Taylor term.
+// col: the amplitude's column in the state planes (row + l * nb), the same
+// for every pulse of a tile row.
 template <bool RK4>
-__device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, df e, df f, float dr, float di,
+__device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, long long col, df e, df f, float dr,
+                                          float di,
                                           const TcIn<RK4> &in)
 {
     const long long q = (long long)b * A.N + a;
@@ -190,8 +193,10 @@ __device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, d
     }
     if (A.gauge) { const float t = dr; dr = -di; di = t; }
     // H x = E x + f D x ;  k = -i H x = (Im, -Re)
-    const df hr = df_add(df_mul(e, xin.re), df_mulf(f, dr));
-    const df hi = df_add(df_mul(e, xin.im), df_mulf(f, di));
+    // f D x in FP32: D x itself comes from bf16x3 products with FP32
+    // accumulation, so a float-float product would add nothing
+    const df hr = df_add(df_mul(e, xin.re), df{__fmul_rn(f.h, dr), 0.f});
+    const df hi = df_add(df_mul(e, xin.im), df{__fmul_rn(f.h, di), 0.f});
     const dfc k{hi, df_neg(hr)};
     dfc out;
     if constexpr (RK4) {
@@ -221,8 +226,6 @@ __device__ __forceinline__ void tc_update(const TcArgs &A, int b, long long a, d
             out = sum;
         }
     }
-    const int l = (int)(a / A.n);
-    const long long col = (a - (long long)l * A.n) + (long long)l * A.nb;
     const long long pr = (2LL * b) * A.plane + col, pi = (2LL * b + 1) * A.plane + col;
     split_bf16(out.re, A.xo_h + pr, A.xo_l + pr);
     split_bf16(out.im, A.xo_h + pi, A.xo_l + pi);
@@ -368,6 +371,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
             tc_fence_after();
             const int row = i0 + quarter * 32 + lane;
             const long long a = (long long)l * n + row;
+            const long long col = (long long)l * A.nb + row;
             const bool valid_row = row < n;
             df e{0.f, 0.f};
             if (valid_row) { const float2 ev = A.Edf[a]; e = df{ev.x, ev.y}; }
@@ -398,7 +402,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
                         for (int u = 0; u < TC_LOAD_GROUP; ++u) {
                             const int jj = g + u;
                             const int b = c0 / 2 + chunk * 8 + jj;
-                            if (b < A.B) tc_update<RK4>(A, b, a, e, df{fv[u].x, fv[u].y}, v[2 * jj], v[2 * jj + 1], in[u]);
+                            if (b < A.B) tc_update<RK4>(A, b, a, col, e, df{fv[u].x, fv[u].y}, v[2 * jj], v[2 * jj + 1], in[u]);
                         }
                     }
                 }
