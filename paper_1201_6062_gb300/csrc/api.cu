@@ -141,6 +141,7 @@ struct tdse_ctx {
     size_t prof_used = 0;               // events in use
     long prof_products = 0;             // block products inside the traced launches
     DevBuf gbar;                        // grid-barrier counter of the persistent stepping launches
+    DevBuf sdots;                       // per-CTA field-gradient partials of the persistent reverse sweep
     int step_ok = -1;                   // whether the plan runs persistently (-1: not yet known)
     long launches = 0;
     ~tdse_ctx()
@@ -1328,6 +1329,35 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
             }
         }
         // reverse stages of the segment's steps
+        if (persistent && ns * (rk4 ? 4 : order) <= (1L << 20)) {
+            CUDA_TRY(ctx->sdots.ensure(sizeof(double) * (size_t)ctx->plan.grid));
+            if (pending.parts) {
+                CUDA_TRY(tdse::launch_flush(pending, s));
+                ctx->launches += 1;
+                pending = tdse::Flush{};
+            }
+            tdse::StepArgs R{};
+            R.reverse = 1;
+            R.ns = (int)ns;
+            R.passes = (int)(ns * (rk4 ? 4 : order));
+            R.mode = rk4 ? tdse::EPI_RK4 : tdse::EPI_TAYLOR;
+            R.order = order;
+            R.hold = taylor_hold;
+            R.sps = sps;
+            R.dt = dt;
+            R.k0 = k0;
+            R.gbar = ctx->gbar.as<unsigned>();
+            R.store = store(0, 0);
+            R.nst = nst;
+            R.ckpt0 = ckpt(j);
+            R.G = ctx->aG.as<double2>();
+            R.dots = ctx->sdots.as<double>();
+            R.grad = grad_field;
+            CUDA_TRY(tdse::launch_mvt_step(ctx->prec, ctx->plan.cfg, ctx->plan.grid, dadj, ctx->plan.segs.as<Seg>(),
+                                           ctx->plan.cta_off.as<int>(), ctx->errw.as<int>(), R, s));
+            ctx->launches += 1;
+            continue;
+        }
         for (long i = ns - 1; i >= 0; --i) {
             const long k = k0 + i;
             for (int q = rk4 ? 3 : order; q >= (rk4 ? 0 : 1); --q) {

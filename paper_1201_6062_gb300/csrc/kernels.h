@@ -65,6 +65,17 @@ struct StepArgs {
     // the step to store[(i+1)*nst] (NULL: none).
     double2 *store;
     int nst;
+    // Adjoint reverse sweep of one checkpoint segment (reverse = 1): the
+    // products are of the cotangent (the launch's sys[0] is the adjoint
+    // descriptor), pass p is reverse stage p of the segment's ns steps
+    // (last step first), the forward stage inputs come from store (and from
+    // ckpt0 for the first stage of the segment's first step), G is the running
+    // dL/dc, and each stage's field-gradient term (per-CTA partials in dots,
+    // summed in fixed order by CTA 0 after the second barrier) is added to grad.
+    int reverse, ns;
+    const double2 *ckpt0;
+    double2 *G;
+    double *dots, *grad;
 };
 // Whether the plan's CTAs can all be resident at once (required: the CTAs
 // wait for one another at the grid barriers).

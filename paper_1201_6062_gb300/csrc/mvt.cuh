@@ -26,6 +26,7 @@
 // once, so that the others give up at their next barrier.
 #pragma once
 #include "kernels.h"
+#include "adj.cuh"
 #include "epi.cuh"
 #include "sync.cuh"
 
@@ -103,6 +104,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
     __shared__ int issued, consumed;
     __shared__ float xmax_sh[NW], xrow_sh[NW];
     __shared__ int xready, go_flag;       // STEP: passes whose stage inputs are written; barrier verdict
+    __shared__ double dot_sh[NW];         // STEP, adjoint: per-warp field-gradient partials
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -409,6 +411,68 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
             // the stage update of this CTA's slice of amplitudes
             const SysDesc &S0 = sys[0];
             const int per = A.mode == EPI_RK4 ? 4 : A.order;
+            if (A.reverse) {
+                // reverse stage q of step k0+i (the segment's last step first)
+                const int i = A.ns - 1 - pass / per;
+                const int q = A.mode == EPI_RK4 ? 3 - pass % per : A.order - pass % per;
+                const int fq = A.mode == EPI_RK4 ? q : q - 1;
+                const SysDesc &Sa = sys[0];
+                const long long Na = Sa.N;
+                AdjArgs aa{};
+                aa.scheme = A.mode == EPI_RK4 ? 0 : 1;
+                aa.stage = q;
+                aa.order = A.order;
+                aa.hold = A.hold;
+                aa.sps = A.sps;
+                aa.k = A.k0 + i;
+                aa.dt = A.dt;
+                aa.fwd = (fq == 0 && i == 0) ? A.ckpt0 : A.store + (size_t)((long long)i * A.nst + fq) * Na;
+                aa.G = A.G;
+                double dot = 0.0;
+                const long long a1 = Na * (blockIdx.x + 1) / gridDim.x;
+#pragma unroll 1
+                for (long long a = Na * blockIdx.x / gridDim.x + tid; a < a1; a += CT) dot += adj_amp<P>(Sa, a, aa);
+                // fixed-order sum over the CTA: lanes, then warps
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, off);
+                if (lane == 0) dot_sh[warp] = dot;
+                named_sync(1, CT);
+                if (tid == 0) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) t += dot_sh[w];
+                    A.dots[blockIdx.x] = t;
+                }
+                if (!grid_sync(A.gbar, (unsigned)(2 * pass + 2) * gridDim.x, abort, err, &go_flag, tid, CT)) break;
+                if (blockIdx.x == 0 && warp == 0) {
+                    // this stage's dL/df term onto the field samples it reads: the
+                    // CTA partials summed by one warp in a fixed order (lane-strided
+                    // sums, then a fixed shuffle tree)
+                    double t = 0.0;
+                    for (unsigned b = lane; b < gridDim.x; b += 32) t += __ldcg(A.dots + b);
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+                    if (lane == 0) {
+                        const int h = A.mode == EPI_RK4 ? (q == 0 ? 0 : (q == 3 ? 2 : 1)) : (A.hold ? 1 : 0);
+                        const long long k = A.k0 + i;
+                        if (A.sps == 2) {
+                            A.grad[2 * k + h] += t;
+                        } else if (h == 0) {
+                            A.grad[k] += t;
+                        } else if (h == 2) {
+                            A.grad[k + 1] += t;
+                        } else {
+                            A.grad[k] += 0.5 * t;
+                            A.grad[k + 1] += 0.5 * t;
+                        }
+                    }
+                }
+                if (tid == 0) {
+                    __threadfence_block();
+                    *(volatile int *)&xready = pass + 1;
+                }
+                continue;
+            }
             EpiArgs e{};
             e.mode = A.mode;
             e.stage = A.mode == EPI_RK4 ? pass % per : pass % per + 1;
