@@ -431,16 +431,32 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs,
 tdse_status tdse_group_sync(tdse_group *g, void *stream);
 
 /*
- * tdse_group_tune — autotuner: for each bucket, times `reps` block-product
- * launches for every valid ring-stage depth (1, 2, 4, 8 rows per bulk copy)
- * on the bucket's own plan and keeps the fastest for later
- * tdse_group_propagate calls.  Reports the depth chosen for the bucket with
- * the most dipole bytes and the summed best time of one product of every
- * system (either pointer may be NULL).  Clobbers
- * the members' scratch vectors; synchronises `stream`.
- * Errors: EINVAL, ECUDA, ETIMEOUT.
+ * tdse_group_tune — autotuner of the block product's tile shape per bucket
+ * (Sec. 4.1 leaves the work-group size to the device; the paper tuned it by
+ * hand per GPU): for every thread layout from the members' own to the next
+ * two wider ones (more column groups per row per CTA) and every valid ring
+ * depth (1, 2, 4, 8 rows per bulk copy) it re-plans the bucket, times `reps`
+ * launches, and keeps the fastest for later tdse_group_propagate calls.
+ * Reports the depth chosen for the bucket with the most dipole bytes and the
+ * summed best time of one product of every system (either pointer may be
+ * NULL).  Clobbers the members' scratch vectors; synchronises `stream`.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT.
  */
 tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *best_ms, void *stream);
+
+/*
+ * Tuning cache.  tdse_group_tuning_save writes, to the text file `path`, one
+ * line per bucket: its precision and members' (lmax, n), then the thread
+ * layout and rows per stage it uses.  tdse_group_tuning_load applies every
+ * line whose bucket matches one of g's (same precision and members, in
+ * order) and still fits, re-planning those buckets, and reports how many it
+ * applied (may be NULL); other lines are ignored.  Host file I/O only; a
+ * re-planned bucket's next propagation captures a new step graph.
+ * Errors: EINVAL (NULL argument, unreadable or unwritable file, not a tuning
+ * file), ENOMEM, ECUDA.
+ */
+tdse_status tdse_group_tuning_save(const tdse_group *g, const char *path);
+tdse_status tdse_group_tuning_load(tdse_group *g, const char *path, int *applied);
 
 /*
  * Failure detection.

@@ -165,7 +165,7 @@ static int sm_count()
 
 // Build the mat-vec plan for the given systems and upload it.
 static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std::vector<int> &n, MvPlan &mp,
-                              tdse::Plan &plan, const std::vector<int> *global_id = nullptr)
+                              tdse::Plan &plan, const std::vector<int> *global_id = nullptr, int layout = -1)
 {
     int nmax = 1;
     long long rows = 0, amps = 0;
@@ -176,7 +176,9 @@ static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std:
     const int ldmax = (nmax + 3) & ~3;
     mp.max_ld = ldmax;
     int G;
-    if (tdse::mvt_config(prec, nmax, ldmax, &mp.cfg)) {
+    const bool ring = layout >= 0 ? tdse::mvt_config_layout(prec, nmax, ldmax, layout, &mp.cfg)
+                                  : tdse::mvt_config(prec, nmax, ldmax, &mp.cfg);
+    if (ring) {
         // Several ring CTAs per SM when short rows leave shared memory for them,
         // but only for dipole blocks streamed from HBM: when they stay in L2,
         // more CTAs only add column-partial slots and per-CTA overhead.
@@ -1395,6 +1397,7 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
 // Systems whose rows take the same thread layout share one product launch.
 struct GroupBucket {
     std::vector<int> members;           // system indices in the group
+    int layout = -1;                    // ring thread layout chosen by the tuner (-1: the members' own)
     long long bytes = 0;                // dipole bytes of one product
     MvPlan plan;                        // work split over all SMs, layout for the bucket's largest n
     int tuned_rs = 0;                   // rows per ring stage chosen by tdse_group_tune (0: default)
@@ -1426,6 +1429,34 @@ struct tdse_group {
         if (stage_ev) cudaEventDestroy(stage_ev);
     }
 };
+
+// (Re)plan bucket b with its layout (the members' own when bk.layout < 0):
+// the work split, each member's column-partial slots and slot starts, and
+// their descriptors.  Any captured step graph is dropped.
+static tdse_status bucket_plan(tdse_group *g, GroupBucket &bk)
+{
+    std::vector<int> blm, bnn;
+    for (int i : bk.members) { blm.push_back(g->sys[i]->lmax); bnn.push_back(g->sys[i]->n); }
+    tdse::Plan plan;
+    tdse_status st = build_plan(g->prec, blm, bnn, bk.plan, plan, &bk.members, bk.layout);
+    if (st != TDSE_OK) return st;
+    for (size_t k = 0; k < bk.members.size(); ++k) {
+        const int i = bk.members[k];
+        tdse_ctx *c = g->sys[i];
+        const size_t ns = (size_t)(plan.nslots[k] > 0 ? plan.nslots[k] : 1);
+        cudaError_t e = g->P[i].ensure(sizeof(double2) * ns * c->n);
+        if (e == cudaSuccess) e = g->sb[i].ensure(sizeof(int) * (c->lmax + 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->sb[i].p, plan.sb[k].data(), sizeof(int) * (c->lmax + 1), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_status(e), "group buffers: %s", cudaGetErrorString(e));
+        SysDesc d = c->desc;
+        d.P = g->P[i].as<double2>();
+        d.sb = g->sb[i].as<int>();
+        g->desc[i] = d;
+    }
+    if (g->gexec) { cudaGraphExecDestroy(g->gexec); g->gexec = nullptr; }
+    return TDSE_OK;
+}
 
 tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **out)
 {
@@ -1472,31 +1503,13 @@ tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **
     const int eb = elem_bytes(g->prec);
     for (size_t b = 0; b < keys.size(); ++b) {
         GroupBucket &bk = g->buckets[b];
-        std::vector<int> blm, bnn;
         for (int i = 0; i < count; ++i)
             if (key[i] == keys[b]) {
                 bk.members.push_back(i);
-                blm.push_back(lm[i]);
-                bnn.push_back(nn[i]);
                 bk.bytes += (long long)lm[i] * nn[i] * nn[i] * eb;
             }
-        tdse::Plan plan;
-        st = build_plan(g->prec, blm, bnn, bk.plan, plan, &bk.members);
+        st = bucket_plan(g, bk);
         if (st != TDSE_OK) return bail(st);
-        for (size_t k = 0; k < bk.members.size(); ++k) {
-            const int i = bk.members[k];
-            tdse_ctx *c = systems[i];
-            const size_t ns = (size_t)(plan.nslots[k] > 0 ? plan.nslots[k] : 1);
-            cudaError_t e = g->P[i].ensure(sizeof(double2) * ns * c->n);
-            if (e == cudaSuccess) e = g->sb[i].ensure(sizeof(int) * (c->lmax + 1));
-            if (e == cudaSuccess)
-                e = cudaMemcpy(g->sb[i].p, plan.sb[k].data(), sizeof(int) * (c->lmax + 1), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) return bail(fail(TDSE_ECUDA, "group buffers: %s", cudaGetErrorString(e)));
-            SysDesc d = c->desc;
-            d.P = g->P[i].as<double2>();
-            d.sb = g->sb[i].as<int>();
-            g->desc[i] = d;
-        }
     }
     cudaError_t e = g->ddesc.ensure(sizeof(SysDesc) * count);
     if (e == cudaSuccess) e = g->errw.ensure(sizeof(int));
@@ -1638,13 +1651,10 @@ tdse_status tdse_group_sync(tdse_group *g, void *stream)
     return TDSE_OK;
 }
 
-tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *best_ms, void *stream)
+// Uploads the members' descriptors with their own scratch as state (for
+// timing products outside a propagation).
+static tdse_status stage_scratch_desc(tdse_group *g, cudaStream_t s)
 {
-    g_err.clear();
-    if (!g) return fail(TDSE_EINVAL, "NULL group");
-    if (reps < 1) reps = 3;
-    cudaStream_t s = (cudaStream_t)stream;
-    // The descriptors must point at valid state buffers: use each system's own scratch.
     if (g->stage_pending) CUDA_TRY(cudaEventSynchronize(g->stage_ev));
     const int count = (int)g->sys.size();
     for (int i = 0; i < count; ++i) {
@@ -1655,6 +1665,18 @@ tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *bes
     CUDA_TRY(cudaMemcpyAsync(g->ddesc.p, g->stage, sizeof(SysDesc) * count, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaEventRecord(g->stage_ev, s));
     g->stage_pending = true;
+    return TDSE_OK;
+}
+
+tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *best_ms, void *stream)
+{
+    g_err.clear();
+    if (!g) return fail(TDSE_EINVAL, "NULL group");
+    if (reps < 1) reps = 3;
+    cudaStream_t s = (cudaStream_t)stream;
+    // The descriptors must point at valid state buffers: use each system's own scratch.
+    tdse_status st = stage_scratch_desc(g, s);
+    if (st != TDSE_OK) return st;
     CUDA_TRY(tdse::launch_prep(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->ddesc.as<SysDesc>(), 1, s));
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
@@ -1662,32 +1684,62 @@ tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *bes
     double total = 0.0;
     int big_rs = 0;
     long long big_bytes = -1;
-    // each bucket's launch is timed alone for every valid ring depth
+    // Each bucket's launch is timed alone for every tile shape: the thread
+    // layout (its members' own and the next two wider ones, i.e. more column
+    // groups per row per CTA) and every valid ring depth (rows per stage);
+    // a new layout re-plans the bucket (work split, partial slots).
     for (GroupBucket &b : g->buckets) {
-        const tdse::MvCfg base = b.plan.cfg;
-        int best = base.RS;
+        b.layout = -1;
+        b.tuned_rs = 0;
+        st = bucket_plan(g, b);
+        if (st == TDSE_OK) st = stage_scratch_desc(g, s);
+        if (st != TDSE_OK) return st;
+        const bool ring = b.plan.cfg.tma != 0;
+        const int natural = b.plan.cfg.idx;
+        int best_layout = -1, best_rs = b.plan.cfg.RS;
         double bestt = 1e300;
-        for (int rs = base.tma ? 1 : 0; rs <= (base.tma ? 8 : 0); rs = rs ? rs * 2 : 1) {
-            tdse::MvCfg cfg = base;
-            if (base.tma) {
-                if (!tdse::mvt_rs_valid(g->prec, cfg, rs, b.plan.max_ld)) continue;
-                cfg.RS = rs;
-            }
-            tdse_status st = bucket_product(g, b, cfg, s);          // warm-up
-            if (st != TDSE_OK) return st;
-            CUDA_TRY(cudaEventRecord(e0, s));
-            for (int r = 0; r < reps; ++r) {
-                st = bucket_product(g, b, cfg, s);
+        const int last = ring ? std::min(natural + 2, tdse::mvt_layouts() - 1) : natural;
+        for (int lay = natural; lay <= last; ++lay) {
+            if (ring && lay != natural) {
+                b.layout = lay;
+                st = bucket_plan(g, b);
+                if (st != TDSE_OK || !b.plan.cfg.tma || b.plan.cfg.idx != lay) {
+                    g_err.clear();
+                    continue;                       // this layout cannot hold the bucket's rows
+                }
+                st = stage_scratch_desc(g, s);
                 if (st != TDSE_OK) return st;
             }
-            CUDA_TRY(cudaEventRecord(e1, s));
-            CUDA_TRY(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms / reps < bestt) { bestt = ms / reps; best = rs; }
-            if (!base.tma) break;
+            const tdse::MvCfg base = b.plan.cfg;
+            for (int rs = ring ? 1 : 0; rs <= (ring ? 8 : 0); rs = rs ? rs * 2 : 1) {
+                tdse::MvCfg cfg = base;
+                if (ring) {
+                    if (!tdse::mvt_rs_valid(g->prec, cfg, rs, b.plan.max_ld)) continue;
+                    cfg.RS = rs;
+                }
+                st = bucket_product(g, b, cfg, s);          // warm-up
+                if (st != TDSE_OK) return st;
+                CUDA_TRY(cudaEventRecord(e0, s));
+                for (int r = 0; r < reps; ++r) {
+                    st = bucket_product(g, b, cfg, s);
+                    if (st != TDSE_OK) return st;
+                }
+                CUDA_TRY(cudaEventRecord(e1, s));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms / reps < bestt) {
+                    bestt = ms / reps;
+                    best_rs = rs;
+                    best_layout = lay == natural ? -1 : lay;
+                }
+                if (!ring) break;
+            }
         }
-        b.tuned_rs = base.tma ? best : 0;
+        b.layout = best_layout;
+        st = bucket_plan(g, b);
+        if (st != TDSE_OK) return st;
+        b.tuned_rs = ring ? best_rs : 0;
         total += bestt;
         if (b.bytes > big_bytes) { big_bytes = b.bytes; big_rs = b.tuned_rs; }
     }
@@ -1697,6 +1749,74 @@ tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *bes
     if (chosen_rs) *chosen_rs = big_rs;
     if (best_ms) *best_ms = total;
     return tdse_group_sync(g, stream);
+}
+
+// The bucket's identity in a tuning file: precision and its members' (lmax, n).
+static std::string bucket_signature(const tdse_group *g, const GroupBucket &b)
+{
+    std::string sig = "prec=" + std::to_string(g->prec) + " members=" + std::to_string(b.members.size());
+    for (int i : b.members) sig += " " + std::to_string(g->sys[i]->lmax) + ":" + std::to_string(g->sys[i]->n);
+    return sig;
+}
+
+tdse_status tdse_group_tuning_save(const tdse_group *g, const char *path)
+{
+    g_err.clear();
+    if (!g || !path) return fail(TDSE_EINVAL, "NULL argument");
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(TDSE_EINVAL, "cannot write %s", path);
+    fprintf(f, "tdse-group-tuning 1\n");
+    for (const GroupBucket &b : g->buckets)
+        fprintf(f, "%s | layout=%d rs=%d\n", bucket_signature(g, b).c_str(), b.plan.cfg.idx, b.tuned_rs);
+    const bool ok = fclose(f) == 0;
+    return ok ? TDSE_OK : fail(TDSE_EINVAL, "cannot write %s", path);
+}
+
+tdse_status tdse_group_tuning_load(tdse_group *g, const char *path, int *applied)
+{
+    g_err.clear();
+    if (applied) *applied = 0;
+    if (!g || !path) return fail(TDSE_EINVAL, "NULL argument");
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(TDSE_EINVAL, "cannot read %s", path);
+    std::vector<std::string> lines;
+    char buf[65536];
+    bool header = false;
+    while (fgets(buf, sizeof buf, f)) {
+        std::string line(buf);
+        while (!line.empty() && (line.back() == '\n' || line.back() == '\r')) line.pop_back();
+        if (!header) { header = line == "tdse-group-tuning 1"; if (!header) break; continue; }
+        lines.push_back(line);
+    }
+    fclose(f);
+    if (!header) return fail(TDSE_EINVAL, "%s is not a tuning file", path);
+    int n = 0;
+    for (GroupBucket &b : g->buckets) {
+        const std::string sig = bucket_signature(g, b) + " | ";
+        for (const std::string &line : lines) {
+            if (line.compare(0, sig.size(), sig) != 0) continue;
+            int lay = -1, rs = 0;
+            if (sscanf(line.c_str() + sig.size(), "layout=%d rs=%d", &lay, &rs) != 2) continue;
+            const int old_layout = b.layout, old_rs = b.tuned_rs;
+            b.layout = lay;
+            tdse_status st = bucket_plan(g, b);
+            const bool fits = st == TDSE_OK && b.plan.cfg.idx == lay &&
+                              (!b.plan.cfg.tma ? rs == 0 : tdse::mvt_rs_valid(g->prec, b.plan.cfg, rs, b.plan.max_ld));
+            if (!fits) {                           // stale entry: keep the bucket as it was
+                g_err.clear();
+                b.layout = old_layout;
+                b.tuned_rs = old_rs;
+                st = bucket_plan(g, b);
+                if (st != TDSE_OK) return st;
+                break;
+            }
+            b.tuned_rs = rs;
+            ++n;
+            break;
+        }
+    }
+    if (applied) *applied = n;
+    return TDSE_OK;
 }
 
 tdse_status tdse_set_device_memory_limit(long long bytes)

@@ -39,6 +39,11 @@ bool mvt_config(int prec, int n, int ld, MvCfg *out);
 int mvt_ctas_per_sm(int prec, const MvCfg &cfg);
 // Sets the kernel attributes a launch needs (call outside stream capture).
 cudaError_t mvt_prepare(int prec, const MvCfg &cfg);
+// As mvt_config with thread layout `idx` forced (false if it cannot hold a
+// row of n columns); mvt_layouts() = number of layouts, ordered by the
+// columns they hold.
+bool mvt_config_layout(int prec, int n, int ld, int idx, MvCfg *out);
+int mvt_layouts(void);
 // Whether `rs` rows per stage fit the ring for rows of `ld` elements.
 bool mvt_rs_valid(int prec, const MvCfg &cfg, int rs, int ld);
 cudaError_t launch_mvt(int prec, const MvCfg &cfg, int grid, const SysDesc *sys, const Seg *segs,

@@ -38,6 +38,23 @@ bool mvt_config(int prec, int n, int ld, MvCfg *out)
     return false;
 }
 
+bool mvt_config_layout(int prec, int n, int ld, int idx, MvCfg *out)
+{
+    MvCfg c{};
+    if (!mvt_config(prec, n, ld, &c)) return false;
+    if (idx < 0 || idx >= kNumTCfg) return false;
+    const int groups = (n + col_width(prec) - 1) / col_width(prec);
+    if (groups > kTCfg[idx].CT * kTCfg[idx].MAXG) return false;
+    *out = MvCfg{idx, kTCfg[idx].CT, 1, kTCfg[idx].MAXG, kTCfg[idx].CT + 32};
+    out->tma = 1;
+    out->RS = c.RS;
+    out->ld = ld;
+    if (!mvt_fn_prec(prec, idx, out->RS)) out->RS = 2;      // the widest layout serves at most 2 rows per stage
+    return mvt_fn_prec(prec, idx, out->RS) != nullptr;
+}
+
+int mvt_layouts(void) { return kNumTCfg; }
+
 bool mvt_rs_valid(int prec, const MvCfg &cfg, int rs, int ld)
 {
     if (rs != 1 && rs != 2 && rs != 4 && rs != 8) return false;

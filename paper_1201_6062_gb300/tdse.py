@@ -332,6 +332,10 @@ _lib.tdse_group_sync.argtypes = [_vp, _vp]
 _lib.tdse_group_sync.restype = _i
 _lib.tdse_group_tune.argtypes = [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]
 _lib.tdse_group_tune.restype = _i
+_lib.tdse_group_tuning_save.argtypes = [_vp, ctypes.c_char_p]
+_lib.tdse_group_tuning_save.restype = _i
+_lib.tdse_group_tuning_load.argtypes = [_vp, ctypes.c_char_p, ctypes.POINTER(_i)]
+_lib.tdse_group_tuning_load.restype = _i
 
 
 class Group:
@@ -386,9 +390,20 @@ class Group:
                                 [x.value for x in v])))
         return out
 
+    def save_tuning(self, path):
+        """Write the buckets' tile shapes (thread layout, rows per stage) to a text file."""
+        _check(_lib.tdse_group_tuning_save(self._g, os.fsencode(path)))
+
+    def load_tuning(self, path):
+        """Apply the matching lines of a tuning file; returns how many buckets were re-planned."""
+        n = _i()
+        _check(_lib.tdse_group_tuning_load(self._g, os.fsencode(path), ctypes.byref(n)))
+        return n.value
+
     def tune(self, reps=3, stream=None):
-        """Autotune the ring-stage depth of every bucket; returns (rows per
-        stage of the bucket with the most bytes, summed ms of one product)."""
+        """Autotune every bucket's tile shape (thread layout and rows per ring
+        stage); returns (rows per stage of the bucket with the most bytes,
+        summed ms of one product)."""
         rs, ms = _i(), _d()
         _check(_lib.tdse_group_tune(self._g, int(reps), ctypes.byref(rs), ctypes.byref(ms), _stream(stream)))
         return rs.value, ms.value

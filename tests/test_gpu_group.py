@@ -89,3 +89,47 @@ def test_group_members_keep_their_gauge(tdse_lib):
         with oracle.gauge("velocity" if q == 1 else "length"):
             ref, _ = oracle.rk4(lmax, n, E, U, c0, F, dt, nsteps)
         assert rel(c.cpu().numpy(), ref) < 1e-10, q
+
+
+def test_tuned_tile_shapes_are_saved_and_reloaded(tdse_lib, tmp_path):
+    """The autotuner picks a thread layout and ring depth per bucket; a second
+    group of the same systems loaded from the saved file takes the same launch
+    shapes and still matches the oracle."""
+    shapes = [(8, 700), (6, 1100), (12, 300), (5, 650)]
+    dt, nsteps = 0.02, 6
+    mem = members(shapes, dt, nsteps, seed0=400)
+    hams = [tdse_lib.Hamiltonian(E, U, lmax, n, "df32") for (lmax, n, E, U, F, c0) in mem]
+    g = tdse_lib.Group(hams)
+    g.tune(reps=2)
+    tuned = g.plan_info()
+    path = str(tmp_path / "tuning.txt")
+    g.save_tuning(path)
+    g.close()
+    g2 = tdse_lib.Group(hams)
+    assert g2.load_tuning(path) == len(tuned)
+    assert g2.plan_info() == tuned
+    cs = [torch.from_numpy(m[5].copy()).cuda() for m in mem]
+    g2.propagate(cs, [torch.from_numpy(m[4]).cuda() for m in mem], dt, nsteps)
+    g2.sync()
+    for (lmax, n, E, U, F, c0), c in zip(mem, cs):
+        ref, _ = oracle.rk4(lmax, n, E, U, c0, F, dt, nsteps)
+        assert rel(c.cpu().numpy(), ref) < 1e-10, (lmax, n)
+    # a file for other systems applies to nothing
+    other = [tdse_lib.Hamiltonian(inputs.energies(3, 500), inputs.dipoles(3, 500, 9), 3, 500, "df32")]
+    g3 = tdse_lib.Group(other)
+    assert g3.load_tuning(path) == 0
+    g2.close()
+    g3.close()
+
+
+def test_tuning_file_errors(tdse_lib, tmp_path):
+    E = inputs.energies(2, 300)
+    H = tdse_lib.Hamiltonian(E, inputs.dipoles(2, 300, 1), 2, 300, "fp32")
+    g = tdse_lib.Group([H])
+    bad = tmp_path / "bad.txt"
+    bad.write_text("not a tuning file\n")
+    with pytest.raises(tdse_lib.TDSEError):
+        g.load_tuning(str(bad))
+    with pytest.raises(tdse_lib.TDSEError):
+        g.load_tuning(str(tmp_path / "missing.txt"))
+    g.close()
