@@ -1562,7 +1562,21 @@ static int group_product_launches(const tdse_group *g)
 
 // Enqueue one RK4 step (4 products + 4 epilogues + the step-counter bump);
 // the epilogues read the step index from g->kdev.
-static tdse_status group_step(tdse_group *g, int sps, double dt, cudaStream_t s)
+// Streams and events that fork a stage's bucket products (independent of
+// one another: each system is in one bucket) and join them before the update.
+struct StageFork {
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t start = nullptr;
+    ~StageFork()
+    {
+        for (cudaStream_t x : streams) cudaStreamDestroy(x);
+        for (cudaEvent_t x : done) cudaEventDestroy(x);
+        if (start) cudaEventDestroy(start);
+    }
+};
+
+static tdse_status group_step(tdse_group *g, int sps, double dt, cudaStream_t s, StageFork *fork = nullptr)
 {
     tdse::EpiArgs a{};
     a.mode = tdse::EPI_RK4;
@@ -1571,8 +1585,20 @@ static tdse_status group_step(tdse_group *g, int sps, double dt, cudaStream_t s)
     a.kdev = g->kdev.as<long long>();
     for (int q = 0; q < 4; ++q) {
         a.stage = q;
-        tdse_status st = group_product(g, s);
-        if (st != TDSE_OK) return st;
+        if (fork) {
+            // the buckets run side by side, so one bucket's tail overlaps the next one's start
+            CUDA_TRY(cudaEventRecord(fork->start, s));
+            for (size_t b = 0; b < g->buckets.size(); ++b) {
+                CUDA_TRY(cudaStreamWaitEvent(fork->streams[b], fork->start, 0));
+                tdse_status st = bucket_product(g, g->buckets[b], bucket_cfg(g->buckets[b]), fork->streams[b]);
+                if (st != TDSE_OK) return st;
+                CUDA_TRY(cudaEventRecord(fork->done[b], fork->streams[b]));
+                CUDA_TRY(cudaStreamWaitEvent(s, fork->done[b], 0));
+            }
+        } else {
+            tdse_status st = group_product(g, s);
+            if (st != TDSE_OK) return st;
+        }
         CUDA_TRY(tdse::launch_epi(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->ddesc.as<SysDesc>(), a, s));
     }
     CUDA_TRY(tdse::launch_bump(g->kdev.as<long long>(), s));
@@ -1618,11 +1644,22 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const dou
         }
         cudaStream_t cs;
         CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        StageFork fork;
+        const bool forked = g->buckets.size() > 1;
+        if (forked) {
+            fork.streams.resize(g->buckets.size());
+            fork.done.resize(g->buckets.size());
+            CUDA_TRY(cudaEventCreateWithFlags(&fork.start, cudaEventDisableTiming));
+            for (size_t b = 0; b < g->buckets.size(); ++b) {
+                CUDA_TRY(cudaStreamCreateWithFlags(&fork.streams[b], cudaStreamNonBlocking));
+                CUDA_TRY(cudaEventCreateWithFlags(&fork.done[b], cudaEventDisableTiming));
+            }
+        }
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         tdse_status st = TDSE_OK;
         if (e == cudaSuccess) {
-            st = group_step(g, samples_per_step, dt, cs);
+            st = group_step(g, samples_per_step, dt, cs, forked ? &fork : nullptr);
             e = cudaStreamEndCapture(cs, &graph);
         }
         if (e == cudaSuccess && st == TDSE_OK) e = cudaGraphInstantiate(&g->gexec, graph, 0);
