@@ -416,10 +416,12 @@ void tdse_group_destroy(tdse_group *g);
 /*
  * c_ptrs[s]      device, complex [N_s] state of system s (in/out).
  * field_ptrs[s]  device, FP64 [samples_per_step*nsteps + 1] field of system s.
- * Both arrays are host arrays of `count` device pointers.  RK4 only.  Each
- * stage is one block-product launch per bucket and one epilogue launch for
- * all systems; one step is captured once into a CUDA graph (re-captured when dt or
- * samples_per_step change) and replayed nsteps times.  The systems' own
+ * Both arrays are host arrays of `count` device pointers.  RK4 only.  One
+ * step is captured once into a CUDA graph (re-captured when dt,
+ * samples_per_step or the buckets' plans change) and replayed nsteps times;
+ * in it every bucket runs its four stages (block product, then its members'
+ * stage update) on a stream of its own, the buckets side by side, joined at
+ * the end of the step.  The systems' own
  * scratch vectors are used, so a context must not be propagated on its own
  * while its group runs.  Errors: EINVAL, ECUDA.
  */

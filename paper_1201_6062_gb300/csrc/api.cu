@@ -1398,6 +1398,8 @@ tdse_status tdse_adjoint(tdse_ctx *ctx, const double *c0, const double *field, i
 struct GroupBucket {
     std::vector<int> members;           // system indices in the group
     int layout = -1;                    // ring thread layout chosen by the tuner (-1: the members' own)
+    DevBuf blk;                         // update block map of its members (blocks of 256 amplitudes)
+    int nblk = 0;
     long long bytes = 0;                // dipole bytes of one product
     MvPlan plan;                        // work split over all SMs, layout for the bucket's largest n
     int tuned_rs = 0;                   // rows per ring stage chosen by tdse_group_tune (0: default)
@@ -1510,6 +1512,14 @@ tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **
             }
         st = bucket_plan(g, bk);
         if (st != TDSE_OK) return bail(st);
+        std::vector<int2> bb;
+        for (int i : bk.members)
+            for (long long a = 0; a < (long long)systems[i]->N; a += 256) bb.push_back(make_int2(i, (int)a));
+        bk.nblk = (int)bb.size();
+        cudaError_t eb2 = bk.blk.ensure(sizeof(int2) * (bb.empty() ? 1 : bb.size()));
+        if (eb2 == cudaSuccess && !bb.empty())
+            eb2 = cudaMemcpy(bk.blk.p, bb.data(), sizeof(int2) * bb.size(), cudaMemcpyHostToDevice);
+        if (eb2 != cudaSuccess) return bail(fail(cuda_status(eb2), "group buffers: %s", cudaGetErrorString(eb2)));
     }
     cudaError_t e = g->ddesc.ensure(sizeof(SysDesc) * count);
     if (e == cudaSuccess) e = g->errw.ensure(sizeof(int));
@@ -1562,8 +1572,8 @@ static int group_product_launches(const tdse_group *g)
 
 // Enqueue one RK4 step (4 products + 4 epilogues + the step-counter bump);
 // the epilogues read the step index from g->kdev.
-// Streams and events that fork a stage's bucket products (independent of
-// one another: each system is in one bucket) and join them before the update.
+// Streams and events that fork the buckets of a step (independent of one
+// another: each system is in one bucket) and join them at its end.
 struct StageFork {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> done;
@@ -1583,23 +1593,32 @@ static tdse_status group_step(tdse_group *g, int sps, double dt, cudaStream_t s,
     a.sps = sps;
     a.dt = dt;
     a.kdev = g->kdev.as<long long>();
-    for (int q = 0; q < 4; ++q) {
-        a.stage = q;
-        if (fork) {
-            // the buckets run side by side, so one bucket's tail overlaps the next one's start
-            CUDA_TRY(cudaEventRecord(fork->start, s));
-            for (size_t b = 0; b < g->buckets.size(); ++b) {
-                CUDA_TRY(cudaStreamWaitEvent(fork->streams[b], fork->start, 0));
-                tdse_status st = bucket_product(g, g->buckets[b], bucket_cfg(g->buckets[b]), fork->streams[b]);
+    if (fork) {
+        // Each bucket runs its four stages (product, then its members' update)
+        // on a stream of its own: a system's update needs only its own
+        // bucket's product, so buckets overlap one another's products and
+        // updates, and join once per step.
+        CUDA_TRY(cudaEventRecord(fork->start, s));
+        for (size_t b = 0; b < g->buckets.size(); ++b) {
+            const GroupBucket &bk = g->buckets[b];
+            cudaStream_t sb = fork->streams[b];
+            CUDA_TRY(cudaStreamWaitEvent(sb, fork->start, 0));
+            for (int q = 0; q < 4; ++q) {
+                a.stage = q;
+                tdse_status st = bucket_product(g, bk, bucket_cfg(bk), sb);
                 if (st != TDSE_OK) return st;
-                CUDA_TRY(cudaEventRecord(fork->done[b], fork->streams[b]));
-                CUDA_TRY(cudaStreamWaitEvent(s, fork->done[b], 0));
+                CUDA_TRY(tdse::launch_epi(g->prec, bk.nblk, bk.blk.as<int2>(), g->ddesc.as<SysDesc>(), a, sb));
             }
-        } else {
+            CUDA_TRY(cudaEventRecord(fork->done[b], sb));
+            CUDA_TRY(cudaStreamWaitEvent(s, fork->done[b], 0));
+        }
+    } else {
+        for (int q = 0; q < 4; ++q) {
+            a.stage = q;
             tdse_status st = group_product(g, s);
             if (st != TDSE_OK) return st;
+            CUDA_TRY(tdse::launch_epi(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->ddesc.as<SysDesc>(), a, s));
         }
-        CUDA_TRY(tdse::launch_epi(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->ddesc.as<SysDesc>(), a, s));
     }
     CUDA_TRY(tdse::launch_bump(g->kdev.as<long long>(), s));
     return TDSE_OK;
@@ -1671,7 +1690,8 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const dou
         g->graph_sps = samples_per_step;
     }
     for (long k = 0; k < nsteps; ++k) CUDA_TRY(cudaGraphLaunch(g->gexec, s));
-    g->launches += 1 + nsteps * (4 * (group_product_launches(g) + 1) + 1);
+    const long updates = g->buckets.size() > 1 ? (long)g->buckets.size() : 1;     // update launches per stage
+    g->launches += 1 + nsteps * (4 * (group_product_launches(g) + updates) + 1);
     return TDSE_OK;
 }
 
