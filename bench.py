@@ -76,11 +76,15 @@ KERNEL_SOURCES = ["paper_1201_6062_gb300/csrc/mvt.cuh", "paper_1201_6062_gb300/c
                   "paper_1201_6062_gb300/csrc/sync.cuh", "paper_1201_6062_gb300/csrc/wait.h"]
 
 
-def profiled_traffic(prec):
-    """DRAM bytes per launch of the block mat-vec from the committed ncu
-    summary, or None when the kernel sources changed since that capture."""
+def profile_file(prec, persistent):
+    return os.path.join(ROOT, "profiles", "mvt_%s%s_large.md" % (prec, "_step" if persistent else ""))
+
+
+def profiled_traffic(prec, persistent):
+    """DRAM bytes per block product of the dominant kernel from the committed
+    ncu summary, or None when the kernel sources changed since that capture."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "mvt_%s_large.md" % prec)
+    path = profile_file(prec, persistent)
     if not os.path.exists(path):
         return None
     fields = {}
@@ -639,16 +643,21 @@ def run_ours(args):
         H.sync()
         mv_ms, mv_n, launches = H.profile_read()
         H.profile(False)
+        persistent = bool(H.plan_info()["persistent"])
         ub = {"fp64": 8, "df32": 8, "fp32": 4}[prec]
         xb = {"fp64": 16, "df32": 16, "fp32": 8}[prec]
-        alg_bytes = lmax * n * n * ub + N * (xb + 16)
+        # U read once and x read once, plus the row sums written once; a
+        # persistent pass also does the RK4 stage update: the state it reads
+        # and writes (c, acc, x and the next input: 64, 80, 80 and 64 bytes per
+        # amplitude over the four stages, 72 on average) instead
+        alg_bytes = lmax * n * n * ub + N * (xb + (72 if persistent else 16))
         mv_avg = mv_ms / max(mv_n, 1)
         res[prec] = {
             "value": whole_job_rate(ws, N * K, ms), "ms_per_step": ms / K, "mv_ms_avg": mv_avg,
             "mv_launches": mv_n, "gpu_launches": launches,
             "mv_gbs": alg_bytes / (mv_avg / 1e3) / 1e9,
             "mv_tflops": 8.0 * lmax * n * n / (mv_avg / 1e3) / 1e12,
-            "alg_bytes_per_launch": alg_bytes,
+            "alg_bytes_per_launch": alg_bytes, "persistent_stepping": persistent,
         }
         H.close()
         del c
@@ -697,9 +706,13 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": p["mv_gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": p["mv_gbs"] / hbm_peak, "traffic": None, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
-    roof["kernel"] = "mvt_kernel<%s> (block mat-vec, bulk-copy ring)" % primary
-    roof["traffic"] = profiled_traffic(primary)
-    roof["traffic_source"] = "profiles/mvt_%s_large.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)" % primary
+    pers = p["persistent_stepping"]
+    roof["kernel"] = ("mvt_kernel<%s, STEP> (persistent RK4 stepping: bulk-copy ring product, grid barrier, stage "
+                      "update, grid barrier per stage; figures per block product)" % primary if pers else
+                      "mvt_kernel<%s> (block mat-vec, bulk-copy ring)" % primary)
+    roof["traffic"] = profiled_traffic(primary, pers)
+    roof["traffic_source"] = (os.path.relpath(profile_file(primary, pers), ROOT) +
+                              " (ncu dram__bytes_read.sum + dram__bytes_write.sum, per block product)")
     roof["alg_bytes_per_launch"] = p["alg_bytes_per_launch"]
 
     e2e = None

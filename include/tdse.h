@@ -365,11 +365,13 @@ tdse_status tdse_profile_read(tdse_ctx *ctx, double *mv_ms, long *mv_launches, l
  * CTAs of one product launch, the ring CTAs the plan places on each SM (1:
  * every CTA holds an SM alone; more when short rows of dipole blocks that
  * stream from HBM leave shared memory for several rings), the threads per
- * CTA, and whether rows stream through the bulk-copy ring (1) or per-thread
- * loads (0).  Any output pointer may be NULL.  A bf16x3 context has no
+ * CTA, whether rows stream through the bulk-copy ring (1) or per-thread
+ * loads (0), and whether RK4 / Taylor propagations run all their stages in
+ * persistent launches (1) or one product and one update launch per stage
+ * (0).  Any output pointer may be NULL.  A bf16x3 context has no
  * single-system product: ENOTSUP.  Errors: EINVAL, ENOTSUP.
  */
-tdse_status tdse_plan_info(const tdse_ctx *ctx, int *ctas, int *ctas_per_sm, int *threads, int *ring);
+tdse_status tdse_plan_info(tdse_ctx *ctx, int *ctas, int *ctas_per_sm, int *threads, int *ring, int *persistent);
 
 /*
  * tdse_populations_noalloc — the populations of tdse_populations for callers

@@ -1026,12 +1026,15 @@ static void plan_shape(const MvPlan &mp, int *ctas, int *ctas_per_sm, int *threa
     if (ring) *ring = mp.cfg.tma;
 }
 
-tdse_status tdse_plan_info(const tdse_ctx *ctx, int *ctas, int *ctas_per_sm, int *threads, int *ring)
+static bool step_capable(tdse_ctx *ctx);
+
+tdse_status tdse_plan_info(tdse_ctx *ctx, int *ctas, int *ctas_per_sm, int *threads, int *ring, int *persistent)
 {
     g_err.clear();
     if (!ctx) return fail(TDSE_EINVAL, "NULL context");
     if (ctx->prec == TDSE_BF16X3) return fail(TDSE_ENOTSUP, "bf16x3 contexts have no single-system product");
     plan_shape(ctx->plan, ctas, ctas_per_sm, threads, ring);
+    if (persistent) *persistent = step_capable(ctx) ? 1 : 0;
     if (ctas_per_sm && !ctx->plan.cfg.tma) {
         // per-thread-load plans: CTAs per SM follow from the grid over the SMs
         const int sms = sm_count();

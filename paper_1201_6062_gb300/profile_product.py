@@ -1,7 +1,12 @@
 """Profiling driver for ncu: repeated block mat-vec launches on one system,
-or (with --batch B) batched RK4 steps of B pulses sharing one Hamiltonian.
+(with --steps S) propagations of S RK4 steps (FP64 and float-float products:
+one persistent stepping launch each), (with --small) the small system's
+one-cluster propagation, or (with --batch B) batched RK4 steps of B pulses
+sharing one Hamiltonian.
 
     python -m paper_1201_6062_gb300.profile_product --prec fp32 --lmax 31 --n 2000
+    python -m paper_1201_6062_gb300.profile_product --prec df32 --lmax 31 --n 2000 --steps 2
+    python -m paper_1201_6062_gb300.profile_product --prec fp64 --small --steps 200
     python -m paper_1201_6062_gb300.profile_product --prec bf16x3 --lmax 15 --n 1000 --batch 256
 
 Builds the library if needed, runs 5 untimed products and then `--reps`
@@ -29,11 +34,15 @@ def main():
     p.add_argument("--n", type=int, default=2000)
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--reps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=0, help="RK4 steps per propagation (0: single products)")
+    p.add_argument("--small", action="store_true", help="the small system (lmax=3, n=50), one-cluster kernel")
     a = p.parse_args()
     build.build()
     from paper_1201_6062_gb300 import inputs, tdse
     if a.batch:
         return batched(a)
+    if a.small or a.steps:
+        return stepped(a)
     E = inputs.energies(a.lmax, a.n)
     U = inputs.dipoles(a.lmax, a.n, a.seed)
     H = tdse.Hamiltonian(E, U, a.lmax, a.n, a.prec)
@@ -52,6 +61,41 @@ def main():
     alg = a.lmax * a.n * a.n * ub + (a.lmax + 1) * a.n * 32
     print("%s lmax=%d n=%d: %.4f ms per product, %.1f GB/s algorithmic (%d bytes per launch)"
           % (a.prec, a.lmax, a.n, ms / nmv, alg / (ms / nmv) / 1e6, alg))
+
+
+def stepped(a):
+    """Propagations of a.steps RK4 steps (5 untimed, then a.reps timed)."""
+    from paper_1201_6062_gb300 import inputs, tdse
+    if a.small:
+        cfg = inputs.small_system()
+        lmax, n, seed, E0, om, dt = cfg["lmax"], cfg["n"], cfg["seed"], cfg["E0"], cfg["omega"], cfg["dt"]
+    else:
+        lmax, n, seed, E0, om, dt = a.lmax, a.n, a.seed, 0.1, 0.5, 0.01
+    steps = a.steps or 200
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, seed)
+    H = tdse.Hamiltonian(E, U, lmax, n, a.prec)
+    F = torch.from_numpy(inputs.field_samples(E0, om, dt, steps, 1, t0=20.0)).cuda()
+    c0 = torch.from_numpy(inputs.ground_state(lmax, n)).cuda()
+    for _ in range(5):
+        c = c0.clone()
+        H.propagate(c, F, dt, steps)
+    torch.cuda.synchronize()
+    H.profile(True)
+    H.profile_read()
+    for _ in range(a.reps):
+        c = c0.clone()
+        H.propagate(c, F, dt, steps)
+    H.sync()
+    ms, nmv, nk = H.profile_read()
+    c = c0.clone()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    H.propagate(c, F, dt, steps)
+    e1.record()
+    e1.synchronize()
+    print("%s lmax=%d n=%d, %d RK4 steps per propagation: %.4f ms per block product (traced), %.2f us per step"
+          % (a.prec, lmax, n, steps, ms / max(nmv, 1), e0.elapsed_time(e1) * 1e3 / steps))
 
 
 def batched(a):

@@ -53,7 +53,7 @@ _SIGS = {
     "tdse_group_create": ([_vp, _i, ctypes.POINTER(_vp)], _i),
     "tdse_group_destroy": ([_vp], None),
     "tdse_group_propagate": ([_vp, _vp, _vp, _i, _d, _l, _vp], _i),
-    "tdse_plan_info": ([_vp] + [ctypes.POINTER(_i)] * 4, _i),
+    "tdse_plan_info": ([_vp] + [ctypes.POINTER(_i)] * 5, _i),
     "tdse_set_device_memory_limit": ([ctypes.c_longlong], _i),
     "tdse_device_memory_in_use": ([], ctypes.c_longlong),
     "tdse_inject_wait_timeout": ([_vp, _l, _vp], _i),
@@ -269,10 +269,10 @@ class Hamiltonian:
         _check(_lib.tdse_inject_wait_timeout(self._h, int(timeout_ns), _stream(stream)))
 
     def plan_info(self):
-        """Launch shape of the block product: dict(ctas, ctas_per_sm, threads, ring)."""
-        v = [_i() for _ in range(4)]
+        """Launch shape of the block product: dict(ctas, ctas_per_sm, threads, ring, persistent)."""
+        v = [_i() for _ in range(5)]
         _check(_lib.tdse_plan_info(self._h, *[ctypes.byref(x) for x in v]))
-        return dict(zip(("ctas", "ctas_per_sm", "threads", "ring"), [x.value for x in v]))
+        return dict(zip(("ctas", "ctas_per_sm", "threads", "ring", "persistent"), [x.value for x in v]))
 
     def adjoint(self, c0, field, dt, nsteps, weights, scheme="rk4", order=4, hold=HOLD_LEFT, samples_per_step=1,
                 checkpoint_every=64, stream=None):
