@@ -13,11 +13,12 @@
 
 namespace tdse {
 
-template <class P>
+// kCG: read R and P through L2 only (in a persistent launch).
+template <class P, bool kCG = false>
 __device__ __forceinline__ double adj_amp(const SysDesc &S, long long a, const AdjArgs &A)
 {
     // u = D g (D Hermitian in either gauge, so the same products serve the adjoint)
-    const double2 u = dx_at<true>(S, a);   // through L2: a persistent launch rewrote R and P
+    const double2 u = dx_at<kCG>(S, a);
     const double ur = u.x, ui = u.y;
     const double2 g = S.x[a];
     const double e = S.E[a];

@@ -28,26 +28,29 @@ __device__ __forceinline__ EpiPre epi_pre(const SysDesc &S, long long a)
 
 // D x at amplitude a: the row sum (blocks below lmax) plus the column
 // partials of block m-1 in slot order; velocity gauge D x = i (R - sum P).
+// kCG: read through L2 only (in a persistent launch other CTAs wrote R and P
+// moments ago); a separate update launch reads them plainly, which lets the
+// compiler batch the loads (3% of an FP32 step).
+template <bool kCG = false>
 __device__ __forceinline__ double2 epi_dx(const SysDesc &S, long long a, const EpiPre &p)
 {
     double rr = 0.0, ri = 0.0, pr = 0.0, pi = 0.0;
-    // through L2 only: in a persistent launch other CTAs wrote these moments ago
     if (p.m < S.lmax) {
-        const double2 r = __ldcg(S.R + a);
+        const double2 r = kCG ? __ldcg(S.R + a) : S.R[a];
         rr = r.x; ri = r.y;
     }
     for (int s = p.b0; s < p.b1; ++s) {
-        const double2 q = __ldcg(S.P + (long long)s * S.n + p.i);
+        const double2 q = kCG ? __ldcg(S.P + (long long)s * S.n + p.i) : S.P[(long long)s * S.n + p.i];
         pr += q.x; pi += q.y;
     }
     if (S.gauge == 0) return make_double2(rr + pr, ri + pi);
     return make_double2(-(ri - pi), rr - pr);
 }
 
-template <class P>
+template <class P, bool kCG = false>
 __device__ __forceinline__ void epi_amp(const SysDesc &S, long long a, const EpiArgs &A, const EpiPre &pre)
 {
-    const double2 dx = epi_dx(S, a, pre);
+    const double2 dx = epi_dx<kCG>(S, a, pre);
     const double dr = dx.x, di = dx.y;
     const double e = pre.e;
     double f;

@@ -431,7 +431,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                 double dot = 0.0;
                 const long long a1 = Na * (blockIdx.x + 1) / gridDim.x;
 #pragma unroll 1
-                for (long long a = Na * blockIdx.x / gridDim.x + tid; a < a1; a += CT) dot += adj_amp<P>(Sa, a, aa);
+                for (long long a = Na * blockIdx.x / gridDim.x + tid; a < a1; a += CT) dot += adj_amp<P, true>(Sa, a, aa);
                 // fixed-order sum over the CTA: lanes, then warps
 #pragma unroll
                 for (int off = 16; off >= 1; off >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, off);
@@ -496,7 +496,7 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
 #pragma unroll 1
             for (long long a = N * blockIdx.x / gridDim.x + tid; a < a1; a += CT) {
                 const EpiPre pre = epi_pre(S0, a);
-                epi_amp<P>(S0, a, e, pre);
+                epi_amp<P, true>(S0, a, e, pre);
             }
             // every input of the next pass is written
             if (!grid_sync(A.gbar, (unsigned)(2 * pass + 2) * gridDim.x, abort, err, &go_flag, tid, CT)) break;
