@@ -207,7 +207,14 @@ static tdse_status build_plan(int prec, const std::vector<int> &lmax, const std:
         G = sm_count() * tdse::mv_ctas_per_sm(prec, mp.cfg);
     }
     if (rows < G) G = (int)(rows > 0 ? rows : 1);
-    tdse::make_plan(G, lmax, n, 32, plan);
+    // A CTA whose rows cross into the next block sets up a second segment
+    // (its x_{l+1} columns, the |x| bounds of the offset sums, one more
+    // partial slot to write): measured at about 8 rows of a float-float
+    // product with 500-element rows (FP32 products, with the same offset
+    // sums, are charged alike) and 1 row of an FP64 one.  Charged only when
+    // CTAs get enough rows for it to matter.
+    const int seg_rows = rows >= 16LL * G ? (prec == TDSE_FP64 ? 1 : 8) : 0;
+    tdse::make_plan(G, lmax, n, 32, plan, seg_rows);
     mp.grid = rows > 0 ? G : 0;
     std::vector<Seg> segs(plan.segs.size());
     for (size_t i = 0; i < segs.size(); ++i) {

@@ -2,13 +2,13 @@
 #include <vector>
 #include "plan.h"
 
-extern "C" int plan_run(int G, int nsys, const int *lmax, const int *n, int row_overhead,
+extern "C" int plan_run(int G, int nsys, const int *lmax, const int *n, int row_overhead, int seg_rows,
                         int *segs_out /* [max_segs][5] */, int max_segs, int *cta_off_out /* [G+1] */,
                         int *sb_out /* concatenated [lmax_s+1] */)
 {
     std::vector<int> L(lmax, lmax + nsys), N(n, n + nsys);
     tdse::Plan p;
-    tdse::make_plan(G, L, N, row_overhead, p);
+    tdse::make_plan(G, L, N, row_overhead, p, seg_rows);
     if ((int)p.segs.size() > max_segs) return -1;
     for (size_t i = 0; i < p.segs.size(); ++i) {
         segs_out[5 * i + 0] = p.segs[i].sys;
