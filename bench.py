@@ -73,7 +73,8 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
 KERNEL_SOURCES = ["paper_1201_6062_gb300/csrc/mvt.cuh", "paper_1201_6062_gb300/csrc/common.cuh",
-                  "paper_1201_6062_gb300/csrc/sync.cuh", "paper_1201_6062_gb300/csrc/wait.h"]
+                  "paper_1201_6062_gb300/csrc/sync.cuh", "paper_1201_6062_gb300/csrc/wait.h",
+                  "paper_1201_6062_gb300/csrc/epi.cuh", "paper_1201_6062_gb300/csrc/adj.cuh"]
 
 
 def profile_file(prec, persistent):
