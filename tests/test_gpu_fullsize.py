@@ -5,7 +5,8 @@
   alternates two tensor-memory accumulators, so a CTA waits for an
   accumulator to drain and flips its barrier phases only when there are more
   than two tiles per SM.  The pulse-sweep shape (lmax=15, n=1000, 256 pulses)
-  has 8 x 4 x 16 = 512 tiles, 3.4 per SM.
+  has 8 x 4 x 16 = 512 tiles, 3.4 per SM: the last round leaves most SMs
+  without a tile.
 - A ring plan places several CTAs on one SM only when its dipole blocks
   stream from HBM (64 MB or more) and its rows are short enough for several
   rings (and their consumers' registers) to share an SM; the plan then picks
@@ -61,6 +62,35 @@ def test_pulse_sweep_shape_matches_oracle_on_sampled_pulses(tdse_lib, prec):
     for b in (0, 1, 63, 64, 100, 127, 128, 191, 200, 254, 255):
         ref, _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, nsteps)
         assert rel(got[b], ref) < TOL[prec], b
+
+
+@pytest.mark.parametrize("lmax,n,B", [(4, 1000, 256), (9, 1000, 160)])
+def test_partial_last_round_of_tiles(tdse_lib, lmax, n, B):
+    # (4, 1000, 256): 160 tiles, 8 in the second round (the last block's
+    # tiles, which have only the lower coupling); (9, 1000, 160): 240 tiles,
+    # 88 in the second round, and the last pulse tile half empty.
+    dt, nsteps = 0.01, 3
+    G = sms()
+    tiles = -(-n // 128) * -(-2 * B // 128) * (lmax + 1)
+    assert G < tiles < 2 * G
+    E = inputs.energies(lmax, n)
+    U = inputs.dipoles(lmax, n, 4)
+    rng = np.random.default_rng(4)
+    E0 = rng.uniform(0.1, 0.4, B)
+    om = rng.uniform(0.3, 0.9, B)
+    F = np.stack([inputs.field_samples(E0[b], om[b], dt, nsteps, 1, cycles=3, t0=5.0) for b in range(B)])
+    C0 = np.stack([inputs.random_state((lmax + 1) * n, 2000 + b) for b in range(B)])
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "bf16x3")
+    c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+    H.propagate_batch(c, torch.from_numpy(F.reshape(-1)).cuda(), B, dt, nsteps)
+    H.sync()
+    got = c.cpu().numpy().reshape(B, -1)
+    H.close()
+    # both ends of both halves of every pulse tile (32 pulses each)
+    picks = sorted({q for t in range(0, B, 64) for q in (t, t + 31, t + 32, t + 63) if q < B})
+    for b in picks:
+        ref, _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, nsteps)
+        assert rel(got[b], ref) < TOL["bf16x3"], b
 
 
 # ------------------------------------- ring plans with several CTAs per SM --
