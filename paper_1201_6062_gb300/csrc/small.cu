@@ -5,8 +5,9 @@
 //
 // When the dipole blocks fit in the shared memory of a few SMs, a multi-CTA
 // product per stage is pure latency: two launches per stage, each moving a
-// few kilobytes.  Here a cluster of SCL CTAs runs every stage of every step
-// in one launch.  CTA r owns a contiguous range of amplitudes; for each
+// few kilobytes.  Here one thread-block cluster runs every stage of every step
+// in one launch (16 CTAs where the GPU can place a cluster that size, the
+// non-portable maximum, else 8).  CTA r owns a contiguous range of amplitudes; for each
 // owned amplitude a = (m, i) it keeps the row U_m[i][:] (row sum) and the
 // column U_{m-1}[:][i] (transposed sum) in its shared memory, contiguous, so
 // the products read shared memory only.  Every CTA holds the whole stage
@@ -25,8 +26,9 @@ namespace tdse {
 
 namespace {
 
-constexpr int SCL = 8;               // CTAs per cluster (portable maximum)
-constexpr int SNT = 128;             // threads per CTA
+constexpr int SCL_WIDE = 16;         // CTAs per cluster where the GPU allows it (non-portable size)
+constexpr int SCL = 8;               // otherwise (the portable maximum)
+constexpr int SNT = 256;             // threads per CTA
 constexpr int SMAXA = 128;           // amplitudes per CTA (at least one thread each)
 constexpr size_t SMEM_MAX = 200 * 1024;
 
@@ -34,11 +36,11 @@ __device__ __forceinline__ double to_uv(double e, PolF64 *) { return e; }
 __device__ __forceinline__ float to_uv(float e, PolF32 *) { return e; }
 __device__ __forceinline__ df to_uv(float2 e, PolDF32 *) { return df{e.x, e.y}; }
 
-__host__ __device__ inline int small_per_cta(long long N) { return (int)((N + SCL - 1) / SCL); }
+__host__ __device__ inline int small_per_cta(long long N, int scl) { return (int)((N + scl - 1) / scl); }
 
-__host__ __device__ inline size_t small_u_bytes(int eb, int n, long long N)
+__host__ __device__ inline size_t small_u_bytes(int eb, int n, long long N, int scl)
 {
-    return ((size_t)2 * small_per_cta(N) * n * eb + 15) & ~(size_t)15;      // rows + columns
+    return ((size_t)2 * small_per_cta(N, scl) * n * eb + 15) & ~(size_t)15;      // rows + columns
 }
 
 }  // namespace
@@ -51,16 +53,17 @@ __global__ void __launch_bounds__(SNT, 1) small_kernel(SmallArgs A)
     using Comp = typename P::Comp;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
+    const int scl = (int)cluster.num_blocks();
     const int tid = threadIdx.x;
     const int lmax = A.lmax, n = A.n;
     const long long N = A.N;
-    const int per = small_per_cta(N);
+    const int per = small_per_cta(N, scl);
     const long long a0 = (long long)rank * per;
     const int nown = (int)(a0 >= N ? 0 : (N - a0 < per ? N - a0 : per));
     Elem *rowU = reinterpret_cast<Elem *>(sm);               // [per][n]: U_m[i][k]
     Elem *colU = rowU + (size_t)per * n;                     // [per][n]: U_{m-1}[k][i]
     unsigned char *xq[2];
-    xq[0] = sm + small_u_bytes((int)sizeof(Elem), n, N);
+    xq[0] = sm + small_u_bytes((int)sizeof(Elem), n, N, scl);
     xq[1] = xq[0] + N * 16;
     const Elem *Ug = reinterpret_cast<const Elem *>(A.U);
     for (long long q = tid; q < (long long)nown * n; q += SNT) {
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(SNT, 1) small_kernel(SmallArgs A)
                 }
                 x = xn;
                 // publish the next input to every CTA of the cluster (team lanes share the stores)
-                for (int r = sub; r < SCL; r += tpa) P::store_xq(cluster.map_shared_rank(xq[buf ^ 1], r), a, xn);
+                for (int r = sub; r < scl; r += tpa) P::store_xq(cluster.map_shared_rank(xq[buf ^ 1], r), a, xn);
             }
             buf ^= 1;
             cluster.sync();
@@ -158,17 +161,18 @@ __global__ void __launch_bounds__(SNT, 1) small_kernel(SmallArgs A)
     if (own && sub == 0) A.c[a] = c;
 }
 
-static size_t small_smem(int prec, int n, long long N)
+static size_t small_smem(int prec, int n, long long N, int scl)
 {
-    return small_u_bytes(prec == 1 ? 4 : 8, n, N) + 2 * (size_t)N * 16;
+    return small_u_bytes(prec == 1 ? 4 : 8, n, N, scl) + 2 * (size_t)N * 16;
 }
 
+// Fits a cluster of the portable size (and so also a wider one).
 bool small_fits(int prec, int lmax, int n, int ld, long long N)
 {
     (void)lmax;
     (void)ld;
-    if (prec < 0 || prec > 2 || N < 1 || small_per_cta(N) > SMAXA) return false;
-    return small_smem(prec, n, N) <= SMEM_MAX;
+    if (prec < 0 || prec > 2 || N < 1 || small_per_cta(N, SCL) > SMAXA) return false;
+    return small_smem(prec, n, N, SCL) <= SMEM_MAX;
 }
 
 cudaError_t launch_small(int prec, const SmallArgs &A, cudaStream_t stream)
@@ -183,17 +187,32 @@ cudaError_t launch_small(int prec, const SmallArgs &A, cudaStream_t stream)
     const cudaError_t e = ensure_dyn_smem(fn, (int)SMEM_MAX);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(SCL);
     cfg.blockDim = dim3(SNT);
-    cfg.dynamicSmemBytes = small_smem(prec, A.n, A.N);
     cfg.stream = stream;
     cudaLaunchAttribute attr1[1];
     attr1[0].id = cudaLaunchAttributeClusterDimension;
-    attr1[0].val.clusterDim.x = SCL;
     attr1[0].val.clusterDim.y = 1;
     attr1[0].val.clusterDim.z = 1;
     cfg.attrs = attr1;
     cfg.numAttrs = 1;
+    auto shape = [&](int scl) {
+        cfg.gridDim = dim3(scl);
+        cfg.dynamicSmemBytes = small_smem(prec, A.n, A.N, scl);
+        attr1[0].val.clusterDim.x = scl;
+    };
+    // The wider cluster halves each SM's share of the products; take it when
+    // the GPU can place one (the check does not launch anything).
+    static int wide_ok[3] = {-1, -1, -1};
+    if (wide_ok[prec] < 0) {
+        int nc = 0;
+        shape(SCL_WIDE);
+        wide_ok[prec] = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+                                cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) == cudaSuccess && nc >= 1
+                            ? 1
+                            : 0;
+        (void)cudaGetLastError();
+    }
+    shape(wide_ok[prec] == 1 && small_smem(prec, A.n, A.N, SCL_WIDE) <= SMEM_MAX ? SCL_WIDE : SCL);
     void *args[] = {(void *)&A};
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
