@@ -402,11 +402,20 @@ tdse_status tdse_populations_noalloc(const double *c, const double *energies, in
                                      void *stream);
 
 /*
- * Uneven batches: several contexts of different (lmax, n) advanced together.
- * The systems are bucketed by the thread layout their row length takes (a
- * handful of classes); each stage is one block-product launch per bucket
- * (the bucket's rows split evenly over the GPU's SMs) and one epilogue
- * launch for all systems.  All contexts must share one precision.
+ * Uneven batches: several contexts of different (lmax, n) advanced together
+ * (paper Sec. 4 products and App. B RK4 for each system; Sec. 4.1 work
+ * split over all of them).  Two ways to run them, chosen by tdse_group_tune
+ * or tdse_group_set_persistent:
+ *  - bucketed (the default): the systems are bucketed by the thread layout
+ *    their row length takes (a handful of classes); each stage is one
+ *    block-product launch per bucket (the bucket's rows split evenly over the
+ *    GPU's SMs) and its members' stage update;
+ *  - one persistent launch: every stage of every step of every system in
+ *    one cooperative launch with one thread layout, the rows of all systems
+ *    split over all SMs; each stage is the block product, a bounded grid
+ *    barrier, the stage update of each CTA's equal slice of all systems'
+ *    amplitudes, and a second barrier.
+ * All contexts must share one precision.
  */
 typedef struct tdse_group tdse_group;
 
@@ -431,6 +440,27 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs,
                                  const double *const *field_ptrs, int samples_per_step,
                                  double dt, long nsteps, void *stream);
 
+/*
+ * tdse_group_set_persistent — on = 1: later propagations run as one
+ * persistent launch (per 2^18 steps) for all systems.  layout: index of the
+ * thread layout (0 .. the library's layout count - 1; -1: the one the
+ * group's largest n takes alone); rows_per_stage: 1, 2, 4 or 8 rows per bulk
+ * copy (0: the plan's own).  Plans the launch (work split, the systems'
+ * column-partial slots) and synchronises the device.  on = 0: back to the
+ * buckets.  Not while a propagation of the group is in flight.
+ * Errors: EINVAL (argument out of range, a depth that does not fit the
+ * layout's stage), ENOTSUP (rows too short for the bulk-copy ring, or the
+ * launch's CTAs cannot all be resident), ENOMEM, ECUDA; on error the group
+ * keeps its previous mode.
+ *
+ * tdse_group_persistent_info — whether the group runs as one launch, and
+ * that launch's CTAs, CTAs per SM, threads per CTA and rows per ring stage
+ * (zeros when it does not).  Any output pointer may be NULL.  Errors: EINVAL.
+ */
+tdse_status tdse_group_set_persistent(tdse_group *g, int on, int layout, int rows_per_stage);
+tdse_status tdse_group_persistent_info(const tdse_group *g, int *on, int *ctas, int *ctas_per_sm, int *threads,
+                                       int *rows_per_stage);
+
 /* As tdse_sync, for a group (also reports the member kernels' timeouts). */
 tdse_status tdse_group_sync(tdse_group *g, void *stream);
 
@@ -441,6 +471,10 @@ tdse_status tdse_group_sync(tdse_group *g, void *stream);
  * two wider ones (more column groups per row per CTA) and every valid ring
  * depth (1, 2, 4, 8 rows per bulk copy) it re-plans the bucket, times `reps`
  * launches, and keeps the fastest for later tdse_group_propagate calls.
+ * Then it times max(reps, 2) whole RK4 steps with the tuned buckets against
+ * one persistent launch (tdse_group_set_persistent) for the thread layout of
+ * the group's largest n and the next two wider ones at every valid depth,
+ * all on zero states and a zero field, and keeps the faster way.
  * Reports the depth chosen for the bucket with the most dipole bytes and the
  * summed best time of one product of every system (either pointer may be
  * NULL).  Clobbers the members' scratch vectors; synchronises `stream`.
@@ -451,10 +485,12 @@ tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *bes
 /*
  * Tuning cache.  tdse_group_tuning_save writes, to the text file `path`, one
  * line per bucket: its precision and members' (lmax, n), then the thread
- * layout and rows per stage it uses.  tdse_group_tuning_load applies every
- * line whose bucket matches one of g's (same precision and members, in
- * order) and still fits, re-planning those buckets, and reports how many it
- * applied (may be NULL); other lines are ignored.  Host file I/O only; a
+ * layout and rows per stage it uses; and one line for the whole group: its
+ * systems' (lmax, n) and whether it runs as one persistent launch, with that
+ * launch's layout and depth.  tdse_group_tuning_load applies every
+ * line whose bucket (or group) matches g's (same precision and members, in
+ * order) and still fits, re-planning those buckets, and reports how many
+ * lines it applied (may be NULL); other lines are ignored.  Host file I/O only; a
  * re-planned bucket's next propagation captures a new step graph.
  * Errors: EINVAL (NULL argument, unreadable or unwritable file, not a tuning
  * file), ENOMEM, ECUDA.

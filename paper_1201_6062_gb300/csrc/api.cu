@@ -1433,6 +1433,15 @@ struct tdse_group {
     cudaGraphExec_t gexec = nullptr;
     double graph_dt = 0.0;
     int graph_sps = 0;
+    // One persistent launch for every system instead (tdse_group_set_persistent,
+    // or the tuner's choice): one thread layout, one work split over all rows,
+    // its own partial slots and descriptors.
+    int persistent = 0;
+    int playout = -1, prs = 0;          // layout (-1: the largest n's own) and rows per stage (0: the plan's)
+    MvPlan pplan;
+    std::vector<DevBuf> pP, psb;
+    std::vector<SysDesc> pdesc;
+    DevBuf pddesc, amp_off, gbar;
     ~tdse_group()
     {
         cudaDeviceSynchronize();
@@ -1467,6 +1476,52 @@ static tdse_status bucket_plan(tdse_group *g, GroupBucket &bk)
         g->desc[i] = d;
     }
     if (g->gexec) { cudaGraphExecDestroy(g->gexec); g->gexec = nullptr; }
+    return TDSE_OK;
+}
+
+// (Re)plan the single persistent launch over all systems with g->playout /
+// g->prs: the work split of every system's rows over all SMs, the systems'
+// partial slots and descriptors for it, and the amplitude offsets of the
+// joint stage update.
+static tdse_status group_persistent_plan(tdse_group *g)
+{
+    const int count = (int)g->sys.size();
+    std::vector<int> lm(count), nn(count), ids(count);
+    for (int i = 0; i < count; ++i) { lm[i] = g->sys[i]->lmax; nn[i] = g->sys[i]->n; ids[i] = i; }
+    tdse::Plan plan;
+    tdse_status st = build_plan(g->prec, lm, nn, g->pplan, plan, &ids, g->playout);
+    if (st != TDSE_OK) return st;
+    if (!g->pplan.cfg.tma || g->pplan.grid <= 0)
+        return fail(TDSE_ENOTSUP, "one launch for the group needs rows long enough for the bulk-copy ring");
+    if (g->prs > 0) {
+        if (!tdse::mvt_rs_valid(g->prec, g->pplan.cfg, g->prs, g->pplan.max_ld))
+            return fail(TDSE_EINVAL, "rows_per_stage=%d does not fit this layout", g->prs);
+        g->pplan.cfg.RS = g->prs;
+    }
+    if (!tdse::mvt_step_fits(g->prec, g->pplan.cfg, g->pplan.grid))
+        return fail(TDSE_ENOTSUP, "the CTAs of one launch for the group cannot all be resident");
+    g->pP.resize(count);
+    g->psb.resize(count);
+    g->pdesc.resize(count);
+    std::vector<long long> off((size_t)count + 1, 0);
+    for (int k = 0; k < count; ++k) {
+        tdse_ctx *c = g->sys[k];
+        const size_t ns = (size_t)(plan.nslots[k] > 0 ? plan.nslots[k] : 1);
+        cudaError_t e = g->pP[k].ensure(sizeof(double2) * ns * c->n);
+        if (e == cudaSuccess) e = g->psb[k].ensure(sizeof(int) * (c->lmax + 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->psb[k].p, plan.sb[k].data(), sizeof(int) * (c->lmax + 1), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_status(e), "group buffers: %s", cudaGetErrorString(e));
+        SysDesc d = c->desc;
+        d.P = g->pP[k].as<double2>();
+        d.sb = g->psb[k].as<int>();
+        g->pdesc[k] = d;
+        off[(size_t)k + 1] = off[(size_t)k] + c->N;
+    }
+    CUDA_TRY(g->pddesc.ensure(sizeof(SysDesc) * count));
+    CUDA_TRY(g->amp_off.ensure(sizeof(long long) * ((size_t)count + 1)));
+    CUDA_TRY(cudaMemcpy(g->amp_off.p, off.data(), sizeof(long long) * ((size_t)count + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(g->gbar.ensure(sizeof(unsigned)));
     return TDSE_OK;
 }
 
@@ -1535,7 +1590,7 @@ tdse_status tdse_group_create(tdse_ctx *const *systems, int count, tdse_group **
     if (e == cudaSuccess) e = g->errw.ensure(sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->errw.p, 0, sizeof(int));
     if (e == cudaSuccess) e = g->kdev.ensure(sizeof(long long));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->stage, sizeof(SysDesc) * count);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->stage, 2 * sizeof(SysDesc) * count);   // both tables
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->stage_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(fail(TDSE_ECUDA, "group set-up: %s", cudaGetErrorString(e)));
     *out = g;
@@ -1634,24 +1689,12 @@ static tdse_status group_step(tdse_group *g, int sps, double dt, cudaStream_t s,
     return TDSE_OK;
 }
 
-tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const double *const *field_ptrs,
-                                 int samples_per_step, double dt, long nsteps, void *stream)
+// The steps of a group propagation whose arguments are checked: one
+// persistent launch for all systems, or the bucketed step graph.
+static tdse_status group_run(tdse_group *g, double *const *c_ptrs, const double *const *field_ptrs,
+                             int samples_per_step, double dt, long nsteps, cudaStream_t s)
 {
-    g_err.clear();
-    if (!g || !c_ptrs || !field_ptrs) return fail(TDSE_EINVAL, "NULL argument");
-    if (samples_per_step != 1 && samples_per_step != 2) return fail(TDSE_EINVAL, "samples_per_step must be 1 or 2");
-    if (!(dt == dt) || dt == 0.0 || dt > 1e300 || dt < -1e300) return fail(TDSE_EINVAL, "dt must be finite and nonzero");
-    if (nsteps < 0) return fail(TDSE_EINVAL, "nsteps must be >= 0");
     const int count = (int)g->sys.size();
-    for (int i = 0; i < count; ++i) {
-        if (!c_ptrs[i] || !field_ptrs[i]) return fail(TDSE_EINVAL, "c_ptrs[%d] or field_ptrs[%d] is NULL", i, i);
-        if (!aligned16(c_ptrs[i])) return fail(TDSE_EINVAL, "c_ptrs[%d] must be 16-byte aligned", i);
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    for (int i = 0; i < count; ++i) {
-        CUDA_TRY(tdse::launch_field_check(field_ptrs[i], (long long)samples_per_step * nsteps + 1, g->errw.as<int>(), s));
-        g->launches += 1;
-    }
     if (g->stage_pending) CUDA_TRY(cudaEventSynchronize(g->stage_ev));
     for (int i = 0; i < count; ++i) {
         g->stage[i] = g->desc[i];
@@ -1659,9 +1702,42 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const dou
         g->stage[i].field = field_ptrs[i];
     }
     CUDA_TRY(cudaMemcpyAsync(g->ddesc.p, g->stage, sizeof(SysDesc) * count, cudaMemcpyHostToDevice, s));
+    if (g->persistent) {
+        for (int i = 0; i < count; ++i) {
+            g->stage[count + i] = g->pdesc[i];
+            g->stage[count + i].c = (double2 *)c_ptrs[i];
+            g->stage[count + i].field = field_ptrs[i];
+        }
+        CUDA_TRY(cudaMemcpyAsync(g->pddesc.p, g->stage + count, sizeof(SysDesc) * count, cudaMemcpyHostToDevice, s));
+    }
     CUDA_TRY(cudaEventRecord(g->stage_ev, s));
     g->stage_pending = true;
     if (nsteps == 0) return TDSE_OK;
+    if (g->persistent) {
+        // every stage of every system in one cooperative launch (per 2^18
+        // steps): product, grid barrier, the stage update of each CTA's slice
+        // of all systems' amplitudes, grid barrier
+        CUDA_TRY(tdse::launch_prep(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->pddesc.as<SysDesc>(), 0, s));
+        g->launches += 1;
+        const long max_steps = (1L << 20) / 4;
+        for (long k0 = 0; k0 < nsteps; k0 += max_steps) {
+            const long ks = std::min(max_steps, nsteps - k0);
+            tdse::StepArgs A{};
+            A.passes = (int)(4 * ks);
+            A.mode = tdse::EPI_RK4;
+            A.order = 4;
+            A.sps = samples_per_step;
+            A.dt = dt;
+            A.k0 = k0;
+            A.gbar = g->gbar.as<unsigned>();
+            A.nsys = count;
+            A.amp_off = g->amp_off.as<long long>();
+            CUDA_TRY(tdse::launch_mvt_step(g->prec, g->pplan.cfg, g->pplan.grid, g->pddesc.as<SysDesc>(),
+                                           g->pplan.segs.as<Seg>(), g->pplan.cta_off.as<int>(), g->errw.as<int>(), A, s));
+            g->launches += 1;
+        }
+        return TDSE_OK;
+    }
     CUDA_TRY(cudaMemsetAsync(g->kdev.p, 0, sizeof(long long), s));
     CUDA_TRY(tdse::launch_prep(g->prec, g->plan.nblk, g->plan.blk.as<int2>(), g->ddesc.as<SysDesc>(), 0, s));
     // One step is captured once into a CUDA graph and replayed nsteps times.
@@ -1705,6 +1781,73 @@ tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const dou
     return TDSE_OK;
 }
 
+tdse_status tdse_group_propagate(tdse_group *g, double *const *c_ptrs, const double *const *field_ptrs,
+                                 int samples_per_step, double dt, long nsteps, void *stream)
+{
+    g_err.clear();
+    if (!g || !c_ptrs || !field_ptrs) return fail(TDSE_EINVAL, "NULL argument");
+    if (samples_per_step != 1 && samples_per_step != 2) return fail(TDSE_EINVAL, "samples_per_step must be 1 or 2");
+    if (!(dt == dt) || dt == 0.0 || dt > 1e300 || dt < -1e300) return fail(TDSE_EINVAL, "dt must be finite and nonzero");
+    if (nsteps < 0) return fail(TDSE_EINVAL, "nsteps must be >= 0");
+    const int count = (int)g->sys.size();
+    for (int i = 0; i < count; ++i) {
+        if (!c_ptrs[i] || !field_ptrs[i]) return fail(TDSE_EINVAL, "c_ptrs[%d] or field_ptrs[%d] is NULL", i, i);
+        if (!aligned16(c_ptrs[i])) return fail(TDSE_EINVAL, "c_ptrs[%d] must be 16-byte aligned", i);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) {
+        CUDA_TRY(tdse::launch_field_check(field_ptrs[i], (long long)samples_per_step * nsteps + 1, g->errw.as<int>(), s));
+        g->launches += 1;
+    }
+    return group_run(g, c_ptrs, field_ptrs, samples_per_step, dt, nsteps, s);
+}
+
+tdse_status tdse_group_set_persistent(tdse_group *g, int on, int layout, int rows_per_stage)
+{
+    g_err.clear();
+    if (!g) return fail(TDSE_EINVAL, "NULL group");
+    if (on != 0 && on != 1) return fail(TDSE_EINVAL, "on must be 0 or 1");
+    if (layout < -1 || layout >= tdse::mvt_layouts()) return fail(TDSE_EINVAL, "layout %d out of range", layout);
+    if (rows_per_stage != 0 && rows_per_stage != 1 && rows_per_stage != 2 && rows_per_stage != 4 && rows_per_stage != 8)
+        return fail(TDSE_EINVAL, "rows_per_stage must be 0, 1, 2, 4 or 8");
+    if (!on) {
+        g->persistent = 0;
+        return TDSE_OK;
+    }
+    if (g->stage_pending) CUDA_TRY(cudaEventSynchronize(g->stage_ev));
+    const int old_layout = g->playout, old_rs = g->prs;
+    g->playout = layout;
+    g->prs = rows_per_stage;
+    const tdse_status st = group_persistent_plan(g);
+    if (st != TDSE_OK) {
+        g->playout = old_layout;
+        g->prs = old_rs;
+        g->persistent = 0;
+        return st;
+    }
+    g->persistent = 1;
+    return TDSE_OK;
+}
+
+tdse_status tdse_group_persistent_info(const tdse_group *g, int *on, int *ctas, int *ctas_per_sm, int *threads,
+                                       int *rows_per_stage)
+{
+    g_err.clear();
+    if (!g) return fail(TDSE_EINVAL, "NULL group");
+    if (on) *on = g->persistent;
+    if (!g->persistent) {
+        if (ctas) *ctas = 0;
+        if (ctas_per_sm) *ctas_per_sm = 0;
+        if (threads) *threads = 0;
+        if (rows_per_stage) *rows_per_stage = 0;
+        return TDSE_OK;
+    }
+    int ring = 0;
+    plan_shape(g->pplan, ctas, ctas_per_sm, threads, &ring);
+    if (rows_per_stage) *rows_per_stage = g->pplan.cfg.RS;
+    return TDSE_OK;
+}
+
 tdse_status tdse_group_sync(tdse_group *g, void *stream)
 {
     if (!g) return fail(TDSE_EINVAL, "NULL group");
@@ -1732,6 +1875,83 @@ static tdse_status stage_scratch_desc(tdse_group *g, cudaStream_t s)
     CUDA_TRY(cudaMemcpyAsync(g->ddesc.p, g->stage, sizeof(SysDesc) * count, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaEventRecord(g->stage_ev, s));
     g->stage_pending = true;
+    return TDSE_OK;
+}
+
+// Whole RK4 steps of the group as it is planned now (after one untimed step),
+// in ms per step.
+static tdse_status time_group_steps(tdse_group *g, double *const *cp, const double *const *fp, int steps,
+                                    cudaEvent_t e0, cudaEvent_t e1, cudaStream_t s, double *ms_per_step)
+{
+    tdse_status st = group_run(g, cp, fp, 1, 0.01, 1, s);
+    if (st != TDSE_OK) return st;
+    CUDA_TRY(cudaEventRecord(e0, s));
+    st = group_run(g, cp, fp, 1, 0.01, steps, s);
+    if (st != TDSE_OK) return st;
+    CUDA_TRY(cudaEventRecord(e1, s));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *ms_per_step = ms / steps;
+    return TDSE_OK;
+}
+
+// The tuner's second half: whole RK4 steps with the tuned buckets (one step
+// graph of per-bucket launches) against one persistent launch for every
+// system, for the thread layout of the largest n and the next two wider
+// ones at every valid ring depth; the faster is kept.  Timed on zero states
+// and a zero field (the work does not depend on the values).
+static tdse_status tune_mode(tdse_group *g, int reps, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t s)
+{
+    const int count = (int)g->sys.size();
+    const int steps = reps < 2 ? 2 : reps;
+    long long amps = 0;
+    int nmax = 1;
+    for (tdse_ctx *c : g->sys) { amps += c->N; nmax = std::max(nmax, c->n); }
+    DevBuf cbuf, fbuf;
+    CUDA_TRY(cbuf.ensure(sizeof(double2) * (size_t)amps));
+    CUDA_TRY(fbuf.ensure(sizeof(double) * ((size_t)steps + 2)));
+    CUDA_TRY(cudaMemsetAsync(cbuf.p, 0, sizeof(double2) * (size_t)amps, s));
+    CUDA_TRY(cudaMemsetAsync(fbuf.p, 0, sizeof(double) * ((size_t)steps + 2), s));
+    std::vector<double *> cp((size_t)count);
+    std::vector<const double *> fp((size_t)count, fbuf.as<double>());
+    long long o = 0;
+    for (int i = 0; i < count; ++i) {
+        cp[(size_t)i] = reinterpret_cast<double *>(cbuf.as<double2>() + o);
+        o += g->sys[(size_t)i]->N;
+    }
+    g->persistent = 0;
+    double best = 1e300;
+    tdse_status st = time_group_steps(g, cp.data(), fp.data(), steps, e0, e1, s, &best);
+    if (st != TDSE_OK) return st;
+    int best_layout = -2, best_rs = 0;                  // -2: the buckets
+    tdse::MvCfg nat{};
+    const int ldmax = (nmax + 3) & ~3;
+    if (tdse::mvt_config(g->prec, nmax, ldmax, &nat)) {
+        const int last = std::min(nat.idx + 2, tdse::mvt_layouts() - 1);
+        for (int lay = nat.idx; lay <= last; ++lay)
+            for (int rs = 1; rs <= 8; rs *= 2) {
+                g->playout = lay;
+                g->prs = rs;
+                if (group_persistent_plan(g) != TDSE_OK) {
+                    g_err.clear();
+                    continue;
+                }
+                g->persistent = 1;
+                double ms = 1e300;
+                st = time_group_steps(g, cp.data(), fp.data(), steps, e0, e1, s, &ms);
+                g->persistent = 0;
+                if (st != TDSE_OK) return st;
+                if (ms < best) { best = ms; best_layout = lay; best_rs = rs; }
+            }
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (best_layout == -2) return TDSE_OK;
+    g->playout = best_layout;
+    g->prs = best_rs;
+    st = group_persistent_plan(g);
+    if (st != TDSE_OK) return st;
+    g->persistent = 1;
     return TDSE_OK;
 }
 
@@ -1810,9 +2030,11 @@ tdse_status tdse_group_tune(tdse_group *g, int reps, int *chosen_rs, double *bes
         total += bestt;
         if (b.bytes > big_bytes) { big_bytes = b.bytes; big_rs = b.tuned_rs; }
     }
+    if (g->gexec) { cudaGraphExecDestroy(g->gexec); g->gexec = nullptr; }
+    st = tune_mode(g, reps, e0, e1, s);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (g->gexec) { cudaGraphExecDestroy(g->gexec); g->gexec = nullptr; }
+    if (st != TDSE_OK) return st;
     if (chosen_rs) *chosen_rs = big_rs;
     if (best_ms) *best_ms = total;
     return tdse_group_sync(g, stream);
@@ -1826,6 +2048,14 @@ static std::string bucket_signature(const tdse_group *g, const GroupBucket &b)
     return sig;
 }
 
+// The whole group's identity: precision and every system's (lmax, n).
+static std::string group_signature(const tdse_group *g)
+{
+    std::string sig = "group prec=" + std::to_string(g->prec) + " systems=" + std::to_string(g->sys.size());
+    for (const tdse_ctx *c : g->sys) sig += " " + std::to_string(c->lmax) + ":" + std::to_string(c->n);
+    return sig;
+}
+
 tdse_status tdse_group_tuning_save(const tdse_group *g, const char *path)
 {
     g_err.clear();
@@ -1835,6 +2065,8 @@ tdse_status tdse_group_tuning_save(const tdse_group *g, const char *path)
     fprintf(f, "tdse-group-tuning 1\n");
     for (const GroupBucket &b : g->buckets)
         fprintf(f, "%s | layout=%d rs=%d\n", bucket_signature(g, b).c_str(), b.plan.cfg.idx, b.tuned_rs);
+    fprintf(f, "%s | persistent=%d layout=%d rs=%d\n", group_signature(g).c_str(), g->persistent,
+            g->persistent ? g->pplan.cfg.idx : -1, g->persistent ? g->pplan.cfg.RS : 0);
     const bool ok = fclose(f) == 0;
     return ok ? TDSE_OK : fail(TDSE_EINVAL, "cannot write %s", path);
 }
@@ -1881,6 +2113,22 @@ tdse_status tdse_group_tuning_load(tdse_group *g, const char *path, int *applied
             ++n;
             break;
         }
+    }
+    // the choice between the buckets and one persistent launch
+    const std::string gsig = group_signature(g) + " | ";
+    for (const std::string &line : lines) {
+        if (line.compare(0, gsig.size(), gsig) != 0) continue;
+        int on = 0, lay = -1, rs = 0;
+        if (sscanf(line.c_str() + gsig.size(), "persistent=%d layout=%d rs=%d", &on, &lay, &rs) != 3) break;
+        if (on == 0) {
+            g->persistent = 0;
+            ++n;
+        } else if (tdse_group_set_persistent(g, 1, lay, rs) == TDSE_OK) {
+            ++n;
+        } else {
+            g_err.clear();                          // stale entry: keep the group as it was
+        }
+        break;
     }
     if (applied) *applied = n;
     return TDSE_OK;

@@ -81,6 +81,11 @@ struct StepArgs {
     const double2 *ckpt0;
     double2 *G;
     double *dots, *grad;
+    // Several systems in one launch (nsys > 1; forward RK4/Taylor only, no
+    // checkpoints or stores): amplitude a of system s is number
+    // amp_off[s] + a of the launch; each CTA updates an equal slice of them.
+    int nsys;
+    const long long *amp_off;   // [nsys + 1]
 };
 // Whether the plan's CTAs can all be resident at once (required: the CTAs
 // wait for one another at the grid barriers).

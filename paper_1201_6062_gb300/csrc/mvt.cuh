@@ -492,11 +492,27 @@ mvt_kernel(const SysDesc *__restrict__ sys, const Seg *__restrict__ segs, const 
                 else
                     e.st_c = A.store + (size_t)((i + 1) * A.nst) * N;
             }
-            const long long a1 = N * (blockIdx.x + 1) / gridDim.x;
+            if (A.nsys > 1) {
+                // this CTA's slice of all systems' amplitudes, system by system
+                const long long T = A.amp_off[A.nsys];
+                const long long g0 = T * blockIdx.x / gridDim.x, g1 = T * (blockIdx.x + 1) / gridDim.x;
+                int si = 0;
+                while (si + 1 < A.nsys && A.amp_off[si + 1] <= g0) ++si;
 #pragma unroll 1
-            for (long long a = N * blockIdx.x / gridDim.x + tid; a < a1; a += CT) {
-                const EpiPre pre = epi_pre(S0, a);
-                epi_amp<P, true>(S0, a, e, pre);
+                for (; si < A.nsys && A.amp_off[si] < g1; ++si) {
+                    const SysDesc &Sx = sys[si];
+                    const long long o = A.amp_off[si];
+                    const long long hi = min(g1, A.amp_off[si + 1]) - o;
+#pragma unroll 1
+                    for (long long a = max(g0, o) - o + tid; a < hi; a += CT) epi_amp<P, true>(Sx, a, e, epi_pre(Sx, a));
+                }
+            } else {
+                const long long a1 = N * (blockIdx.x + 1) / gridDim.x;
+#pragma unroll 1
+                for (long long a = N * blockIdx.x / gridDim.x + tid; a < a1; a += CT) {
+                    const EpiPre pre = epi_pre(S0, a);
+                    epi_amp<P, true>(S0, a, e, pre);
+                }
             }
             // every input of the next pass is written
             if (!grid_sync(A.gbar, (unsigned)(2 * pass + 2) * gridDim.x, abort, err, &go_flag, tid, CT)) break;

@@ -58,6 +58,8 @@ _SIGS = {
     "tdse_device_memory_in_use": ([], ctypes.c_longlong),
     "tdse_inject_wait_timeout": ([_vp, _l, _vp], _i),
     "tdse_group_plan_info": ([_vp, _i] + [ctypes.POINTER(_i)] * 7, _i),
+    "tdse_group_set_persistent": ([_vp, _i, _i, _i], _i),
+    "tdse_group_persistent_info": ([_vp] + [ctypes.POINTER(_i)] * 5, _i),
 }
 class _FieldFn(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("E0", ctypes.c_double), ("omega", ctypes.c_double),
@@ -340,10 +342,11 @@ _lib.tdse_group_tuning_load.restype = _i
 
 class Group:
     """Several Hamiltonians of different (lmax, n) advanced together (uneven
-    batch): per stage one product launch per thread-layout bucket and one
-    update launch for all, one RK4 step replayed as a CUDA graph.  The member
-    Hamiltonians must outlive the group and must not be propagated on their
-    own while the group runs (their scratch vectors are shared)."""
+    batch): per stage one product launch per thread-layout bucket and its
+    members' update, one RK4 step replayed as a CUDA graph; or (tune() or
+    set_persistent()) every stage of every system in one persistent launch.
+    The member Hamiltonians must outlive the group and must not be propagated
+    on their own while the group runs (their scratch vectors are shared)."""
 
     def __init__(self, hams):
         self.hams = list(hams)
@@ -390,6 +393,18 @@ class Group:
                                 [x.value for x in v])))
         return out
 
+    def set_persistent(self, on=True, layout=-1, rows_per_stage=0):
+        """Run later propagations as one persistent launch for all systems
+        (on=True; layout -1: the largest n's own, rows_per_stage 0: the
+        plan's), or bucketed (on=False)."""
+        _check(_lib.tdse_group_set_persistent(self._g, 1 if on else 0, int(layout), int(rows_per_stage)))
+
+    def persistent_info(self):
+        """dict(on, ctas, ctas_per_sm, threads, rows_per_stage) of the single launch (zeros when bucketed)."""
+        v = [_i() for _ in range(5)]
+        _check(_lib.tdse_group_persistent_info(self._g, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("on", "ctas", "ctas_per_sm", "threads", "rows_per_stage"), [x.value for x in v]))
+
     def save_tuning(self, path):
         """Write the buckets' tile shapes (thread layout, rows per stage) to a text file."""
         _check(_lib.tdse_group_tuning_save(self._g, os.fsencode(path)))
@@ -402,8 +417,9 @@ class Group:
 
     def tune(self, reps=3, stream=None):
         """Autotune every bucket's tile shape (thread layout and rows per ring
-        stage); returns (rows per stage of the bucket with the most bytes,
-        summed ms of one product)."""
+        stage), then keep the buckets or one persistent launch, whichever runs
+        whole RK4 steps faster; returns (rows per stage of the bucket with the
+        most bytes, summed ms of one product)."""
         rs, ms = _i(), _d()
         _check(_lib.tdse_group_tune(self._g, int(reps), ctypes.byref(rs), ctypes.byref(ms), _stream(stream)))
         return rs.value, ms.value

@@ -1,5 +1,7 @@
-"""Uneven batches: systems of different (lmax, n) in one launch per stage,
-each against the oracle (tolerances as for single systems)."""
+"""Uneven batches: systems of different (lmax, n) advanced together, bucketed
+(one product launch per thread-layout bucket and stage) or in one persistent
+launch for all, each system against the oracle (tolerances as for single
+systems)."""
 import numpy as np
 import pytest
 import torch
@@ -102,12 +104,14 @@ def test_tuned_tile_shapes_are_saved_and_reloaded(tdse_lib, tmp_path):
     g = tdse_lib.Group(hams)
     g.tune(reps=2)
     tuned = g.plan_info()
+    mode = g.persistent_info()
     path = str(tmp_path / "tuning.txt")
     g.save_tuning(path)
     g.close()
     g2 = tdse_lib.Group(hams)
-    assert g2.load_tuning(path) == len(tuned)
+    assert g2.load_tuning(path) == len(tuned) + 1          # the buckets and the whole group's mode
     assert g2.plan_info() == tuned
+    assert g2.persistent_info() == mode
     cs = [torch.from_numpy(m[5].copy()).cuda() for m in mem]
     g2.propagate(cs, [torch.from_numpy(m[4]).cuda() for m in mem], dt, nsteps)
     g2.sync()
@@ -132,4 +136,95 @@ def test_tuning_file_errors(tdse_lib, tmp_path):
         g.load_tuning(str(bad))
     with pytest.raises(tdse_lib.TDSEError):
         g.load_tuning(str(tmp_path / "missing.txt"))
+    g.close()
+
+
+# ------------------------------------------- one persistent launch for all --
+
+SHAPES = [(4, 300), (7, 517), (2, 1000), (0, 50), (5, 40), (3, 1500)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df32", "fp32"])
+def test_one_persistent_launch_matches_oracle_per_system(tdse_lib, prec):
+    """Every stage of every system in one cooperative launch with the largest
+    n's thread layout (short rows, a system without blocks and one of a
+    single block included), then back to the buckets."""
+    dt, nsteps = 0.02, 30
+    mem = members(SHAPES, dt, nsteps)
+    hams = [tdse_lib.Hamiltonian(E, U, lmax, n, prec) for (lmax, n, E, U, F, c0) in mem]
+    g = tdse_lib.Group(hams)
+    assert g.persistent_info()["on"] == 0
+    g.set_persistent(True)
+    info = g.persistent_info()
+    assert info["on"] == 1 and info["ctas"] > 0 and info["rows_per_stage"] in (1, 2, 4, 8)
+    fs = [torch.from_numpy(m[4]).cuda() for m in mem]
+    refs = [oracle.rk4(lmax, n, E, U, c0, F, dt, nsteps)[0] for (lmax, n, E, U, F, c0) in mem]
+    cs = [torch.from_numpy(m[5].copy()).cuda() for m in mem]
+    g.propagate(cs, fs, dt, nsteps)
+    g.sync()
+    for m, c, ref in zip(mem, cs, refs):
+        assert rel(c.cpu().numpy(), ref) < TOL[prec], m[:2]
+    g.set_persistent(False)
+    assert g.persistent_info() == dict(on=0, ctas=0, ctas_per_sm=0, threads=0, rows_per_stage=0)
+    cs = [torch.from_numpy(m[5].copy()).cuda() for m in mem]
+    g.propagate(cs, fs, dt, nsteps)
+    g.sync()
+    for m, c, ref in zip(mem, cs, refs):
+        assert rel(c.cpu().numpy(), ref) < TOL[prec], m[:2]
+    g.close()
+
+
+def test_one_persistent_launch_every_layout_and_depth(tdse_lib):
+    """Every thread layout that holds the longest row, at every ring depth
+    that fits its stage: the same results."""
+    dt, nsteps = 0.02, 8
+    shapes = [(6, 700), (3, 1200), (9, 400), (2, 90)]
+    mem = members(shapes, dt, nsteps, seed0=500)
+    hams = [tdse_lib.Hamiltonian(E, U, lmax, n, "df32") for (lmax, n, E, U, F, c0) in mem]
+    g = tdse_lib.Group(hams)
+    fs = [torch.from_numpy(m[4]).cuda() for m in mem]
+    refs = [oracle.rk4(lmax, n, E, U, c0, F, dt, nsteps)[0] for (lmax, n, E, U, F, c0) in mem]
+    ran = set()
+    for layout in range(12):
+        for rs in (1, 2, 4, 8):
+            try:
+                g.set_persistent(True, layout=layout, rows_per_stage=rs)
+            except tdse_lib.TDSEError as e:
+                assert e.status in (tdse_lib.EINVAL, tdse_lib.ENOTSUP), str(e)
+                continue
+            info = g.persistent_info()
+            assert info["on"] == 1 and info["rows_per_stage"] == rs
+            ran.add((info["threads"], rs))
+            cs = [torch.from_numpy(m[5].copy()).cuda() for m in mem]
+            g.propagate(cs, fs, dt, nsteps)
+            g.sync()
+            for m, c, ref in zip(mem, cs, refs):
+                assert rel(c.cpu().numpy(), ref) < 1e-10, (layout, rs, m[:2])
+    # n = 1200 float-float rows (600 column pairs) fit the (256, 3), (256, 4)
+    # and (512, 4) layouts; the widest takes at most 2 rows per stage
+    assert len({t for t, _ in ran}) >= 2 and len(ran) >= 5, ran
+    g.close()
+
+
+def test_one_persistent_launch_errors(tdse_lib):
+    E = inputs.energies(2, 300)
+    H = tdse_lib.Hamiltonian(E, inputs.dipoles(2, 300, 1), 2, 300, "df32")
+    g = tdse_lib.Group([H])
+    for bad in (dict(layout=99), dict(layout=-2), dict(rows_per_stage=3)):
+        with pytest.raises(tdse_lib.TDSEError) as ex:
+            g.set_persistent(True, **bad)
+        assert ex.value.status == tdse_lib.EINVAL
+        assert g.persistent_info()["on"] == 0
+    g.set_persistent(True, rows_per_stage=2)
+    with pytest.raises(tdse_lib.TDSEError):
+        g.set_persistent(True, rows_per_stage=3)
+    assert g.persistent_info()["rows_per_stage"] == 2           # a failed call keeps the previous plan
+    g.close()
+    # rows too short for the bulk-copy ring
+    Hs = [tdse_lib.Hamiltonian(inputs.energies(l, n), inputs.dipoles(l, n, 3), l, n, "df32") for l, n in ((3, 40), (2, 50))]
+    g = tdse_lib.Group(Hs)
+    with pytest.raises(tdse_lib.TDSEError) as ex:
+        g.set_persistent(True)
+    assert ex.value.status == tdse_lib.ENOTSUP
+    assert g.persistent_info()["on"] == 0
     g.close()
