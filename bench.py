@@ -446,11 +446,13 @@ def schemes_section(args):
 def uneven_section(args):
     """64 systems of different (lmax, n) (lmax 4..32, n 200..1500, each its own
     pulse) advanced together by tdse_group_propagate: RK4 amplitude-updates/s
-    with FP32, float-float and FP64 products after the ring-depth autotuner,
-    the product bandwidth (and for FP64, bound by the FP64 pipe, its FLOP
-    rate), and the error on the two smallest members over the timed window
-    against the single-system FP64 path (itself checked against the oracle by
-    the tests)."""
+    with FP32, float-float and FP64 products after the autotuner (each
+    bucket's thread layout and ring depth, then buckets or one persistent
+    launch for all systems), the product bandwidth (and for FP64, bound by the
+    FP64 pipe, its FLOP rate), the way the tuner kept and the time per step of
+    the single launch when it kept the buckets, and the error on the two
+    smallest members over the timed window against the single-system FP64
+    path (itself checked against the oracle by the tests)."""
     import torch
     from paper_1201_6062_gb300 import inputs, tdse
     mem = inputs.uneven_batch(64)
@@ -483,9 +485,7 @@ def uneven_section(args):
     amps = sum((m["lmax"] + 1) * m["n"] for m in mem)
     out = {"workload": "uneven batch: 64 systems, lmax 4..32, n 200..1500 (default_rng(4)), %.3e dipole elements, "
                        "RK4 dt=0.01, window t=20..20.12 a.u." % elems, "systems": len(mem), "amplitudes": amps}
-    for p in precs:
-        g = tdse.Group(hams[p])
-        rs, tune_ms = g.tune(3)
+    def window(g):
         cs = [torch.from_numpy(c.copy()).cuda() for c in C0]
         fw = [torch.from_numpy(f[:W + 1].copy()).cuda() for f in F]
         ft = [torch.from_numpy(f[W:].copy()).cuda() for f in F]
@@ -498,13 +498,29 @@ def uneven_section(args):
         e1.record()
         e1.synchronize()
         g.sync()
-        ms = e0.elapsed_time(e1) / K
+        return e0.elapsed_time(e1) / K, cs
+
+    for p in precs:
+        g = tdse.Group(hams[p])
+        rs, tune_ms = g.tune(3)
+        mode = g.persistent_info()
+        # the other way to run the group, for the record: one persistent
+        # launch for all systems (the largest n's layout) when the tuner kept
+        # the buckets
+        other_ms = None
+        if not mode["on"]:
+            g.set_persistent(True)
+            other_ms, _ = window(g)
+            g.set_persistent(False)
+        ms, cs = window(g)
         err = 0.0
         for i in small:
             ref = refs[i]
             err = max(err, float(np.linalg.norm(cs[i].cpu().numpy() - ref) / np.linalg.norm(ref)))
         eb = 4 if p == "fp32" else 8
         out[p] = {"value": amps / (ms / 1e3), "ms_per_step": ms, "product_gbs": 4 * elems * eb / (ms / 1e3) / 1e9,
+                  "tuned_mode": "one persistent launch" if mode["on"] else "buckets",
+                  "one_launch_ms_per_step": other_ms,
                   "tuned_rows_per_stage_largest_bucket": rs, "tuned_ms_per_product": tune_ms,
                   "err_vs_fp64_max": err, "sampled_systems": small}
         if p == "fp64":
