@@ -499,6 +499,18 @@ tdse_status tdse_group_tuning_save(const tdse_group *g, const char *path);
 tdse_status tdse_group_tuning_load(tdse_group *g, const char *path, int *applied);
 
 /*
+ * tdse_set_batch_persistent — bf16x3 contexts: on = 1 (the default) runs
+ * every stage of a tdse_propagate_batch call in one cooperative launch (per
+ * 2^20 stages), each CTA walking its output tiles stage after stage; a tile
+ * of the next stage starts once every tile of the previous stage in the two
+ * blocks it reads (for its pulse columns) has written its state planes
+ * (per-(block, column tile) counters with bounded waits; the planes rotate
+ * through four buffers).  on = 0: one launch per stage.  Both give the same
+ * results bit for bit.  Errors: EINVAL, ENOTSUP (not a bf16x3 context).
+ */
+tdse_status tdse_set_batch_persistent(tdse_ctx *ctx, int on);
+
+/*
  * Failure detection.
  *
  * tdse_set_device_memory_limit caps the device memory that all contexts and

@@ -124,11 +124,13 @@ struct tdse_ctx {
     // RKF 4(5): stage derivatives k_1..k_5, the candidate state, partial sums, controller
     DevBuf rkK, rkY, rkparts, rkctrl;
     // bf16x3 tensor-core path: dipole planes, energies as float-float, float-float
-    // states, double-buffered bf16 state planes and their TMA descriptors
-    DevBuf tU, tEdf, tc_c, tc_x, tc_acc, tc_planes, tc_fdf;
+    // states, TC_NBUF buffers of bf16 state planes and their TMA descriptors,
+    // and the counters of the persistent launch
+    DevBuf tU, tEdf, tc_c, tc_x, tc_acc, tc_planes, tc_fdf, tc_cnt;
     int nb = 0, ldb = 0;
     int tc_B = 0;                       // batch size the plane buffers / maps were built for
-    tdse::TcMaps tc_maps[2];            // [input buffer]
+    tdse::TcMaps tc_maps{};
+    int tc_persistent = 1;              // all stages of a batch in one launch (tdse_set_batch_persistent)
     MvPlan plan;
     SysDesc desc{};                    // host copy of the descriptor (static fields filled)
     SysDesc *stage = nullptr;          // pinned staging for descriptor uploads (2 slots)
@@ -308,11 +310,11 @@ static tdse_status create_tc(tdse_ctx *c, const double *energies, const double *
     const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)(lmax > 0 ? lmax : 1)};
     const cuuint64_t strides[2] = {(cuuint64_t)c->ldb * 2, (cuuint64_t)n * c->ldb * 2};
     const cuuint32_t box[3] = {64, 128, 1};
-    for (int b = 0; b < 2; ++b) {
-        tdse_status st = make_map(&c->tc_maps[b].Uh, dU, 3, dims, strides, box);
-        if (st == TDSE_OK) st = make_map(&c->tc_maps[b].Ul, dU + plane, 3, dims, strides, box);
-        if (st == TDSE_OK) st = make_map(&c->tc_maps[b].Th, dU + 2 * plane, 3, dims, strides, box);
-        if (st == TDSE_OK) st = make_map(&c->tc_maps[b].Tl, dU + 3 * plane, 3, dims, strides, box);
+    {
+        tdse_status st = make_map(&c->tc_maps.Uh, dU, 3, dims, strides, box);
+        if (st == TDSE_OK) st = make_map(&c->tc_maps.Ul, dU + plane, 3, dims, strides, box);
+        if (st == TDSE_OK) st = make_map(&c->tc_maps.Th, dU + 2 * plane, 3, dims, strides, box);
+        if (st == TDSE_OK) st = make_map(&c->tc_maps.Tl, dU + 3 * plane, 3, dims, strides, box);
         if (st != TDSE_OK) return st;
     }
     CUDA_TRY(c->sys.ensure(2 * sizeof(SysDesc)));
@@ -337,16 +339,17 @@ static tdse_status propagate_batch_tc(tdse_ctx *ctx, double *c, const double *fi
         CUDA_TRY(ctx->tc_x.ensure(sizeof(float4) * (size_t)B * N));
         CUDA_TRY(ctx->tc_acc.ensure(sizeof(float4) * (size_t)B * N));
         const size_t pb = sizeof(__nv_bfloat16) * 2 * (size_t)B * plane;      // one (h or l) plane set
-        CUDA_TRY(ctx->tc_planes.ensure(4 * pb));
-        CUDA_TRY(cudaMemsetAsync(ctx->tc_planes.p, 0, 4 * pb, s));                // padding columns stay zero
+        CUDA_TRY(ctx->tc_planes.ensure(2 * tdse::TC_NBUF * pb));
+        CUDA_TRY(cudaMemsetAsync(ctx->tc_planes.p, 0, 2 * tdse::TC_NBUF * pb, s));   // padding columns stay zero
+        CUDA_TRY(ctx->tc_cnt.ensure(sizeof(int) * (size_t)tdse::tc_pipe_counters(ctx->lmax, B)));
         __nv_bfloat16 *base = ctx->tc_planes.as<__nv_bfloat16>();
         const cuuint64_t dims[2] = {(cuuint64_t)plane, (cuuint64_t)(2 * B)};
         const cuuint64_t strides[1] = {(cuuint64_t)plane * 2};
         const cuuint32_t box[2] = {64, (cuuint32_t)tdse::TC_TBN};
-        for (int b = 0; b < 2; ++b) {
-            tdse_status st = make_map(&ctx->tc_maps[b].Xh, base + (size_t)(2 * b) * 2 * B * plane, 2, dims, strides, box);
+        for (int b = 0; b < tdse::TC_NBUF; ++b) {
+            tdse_status st = make_map(&ctx->tc_maps.Xh[b], base + (size_t)(2 * b) * 2 * B * plane, 2, dims, strides, box);
             if (st == TDSE_OK)
-                st = make_map(&ctx->tc_maps[b].Xl, base + (size_t)(2 * b + 1) * 2 * B * plane, 2, dims, strides, box);
+                st = make_map(&ctx->tc_maps.Xl[b], base + (size_t)(2 * b + 1) * 2 * B * plane, 2, dims, strides, box);
             if (st != TDSE_OK) return st;
         }
         ctx->tc_B = B;
@@ -382,6 +385,29 @@ static tdse_status propagate_batch_tc(tdse_ctx *ctx, double *c, const double *fi
     A.x = ctx->tc_x.as<float4>();
     A.acc = ctx->tc_acc.as<float4>();
     A.err = ctx->errw.as<int>();
+    const int per = scheme == TDSE_RK4 ? 4 : order;
+    if (ctx->tc_persistent && tdse::tc_pipe_fits(ctx->n, ctx->lmax, B)) {
+        // every stage in one cooperative launch per 2^20 stages; a tile of
+        // the next stage starts once the tiles it reads have finished
+        A.per = per;
+        A.dt = dt;
+        A.fdf_all = ctx->tc_fdf.as<float2>();
+        for (int b = 0; b < tdse::TC_NBUF; ++b) {
+            A.xh[b] = plane_h(b);
+            A.xl[b] = plane_l(b);
+        }
+        A.cnt = ctx->tc_cnt.as<int>();
+        const long long total = (long long)nsteps * per;
+        for (long long t0 = 0; t0 < total; t0 += (1LL << 20)) {
+            A.t0 = t0;
+            A.nst = (int)std::min<long long>(1LL << 20, total - t0);
+            CUDA_TRY(tdse::launch_tc_pipe(ctx->tc_maps, A, s));
+            ctx->launches += 1;
+        }
+        CUDA_TRY(tdse::launch_tc_out(ctx->tc_c.as<float4>(), (double2 *)c, N * B, s));
+        ctx->launches += 1;
+        return TDSE_OK;
+    }
     long t = 0;
     for (long k = 0; k < nsteps; ++k) {
         A.k = k;
@@ -392,9 +418,10 @@ static tdse_status propagate_batch_tc(tdse_ctx *ctx, double *c, const double *fi
             const int h = scheme == TDSE_RK4 ? (q == 0 ? 0 : (q == 3 ? 2 : 1)) : (hold ? 1 : 0);
             A.fdf = ctx->tc_fdf.as<float2>() + ((size_t)k * 3 + h) * B;
             const int in = (int)(t & 1);
+            A.xin = in;
             A.xo_h = plane_h(in ^ 1);
             A.xo_l = plane_l(in ^ 1);
-            CUDA_TRY(tdse::launch_tc(ctx->tc_maps[in], A, s));
+            CUDA_TRY(tdse::launch_tc(ctx->tc_maps, A, s));
             ctx->launches += 1;
             ++t;
         }
@@ -2131,6 +2158,16 @@ tdse_status tdse_group_tuning_load(tdse_group *g, const char *path, int *applied
         break;
     }
     if (applied) *applied = n;
+    return TDSE_OK;
+}
+
+tdse_status tdse_set_batch_persistent(tdse_ctx *ctx, int on)
+{
+    g_err.clear();
+    if (!ctx) return fail(TDSE_EINVAL, "NULL context");
+    if (on != 0 && on != 1) return fail(TDSE_EINVAL, "on must be 0 or 1");
+    if (ctx->prec != TDSE_BF16X3) return fail(TDSE_ENOTSUP, "only bf16x3 batches run on the tensor cores");
+    ctx->tc_persistent = on;
     return TDSE_OK;
 }
 

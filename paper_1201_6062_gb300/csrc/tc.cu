@@ -243,11 +243,33 @@ constexpr int TC_LOAD_GROUP = 4;                   // pulses whose state loads a
                                                    // tiles beat 32-pulse ones, 0.49 vs 0.57 ms a step)
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // producer, MMA issuer, epilogue
 
-template <bool RK4>
+__device__ __forceinline__ int ld_acquire_int(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Persistent launch: wait (bounded) until *c reaches need; false on a
+// timeout here or elsewhere.
+__device__ __forceinline__ bool wait_count(const int *c, int need, volatile int *abort, const int *err)
+{
+    const uint64_t t0 = globaltimer_ns();
+    while (ld_acquire_int(c) < need) {
+        if (*abort || (*(volatile const int *)err & kErrTimeout) != 0 || globaltimer_ns() - t0 > TC_WAIT_NS)
+            return false;
+    }
+    return true;
+}
+
+// PIPE = false: one stage per launch, input planes in buffer A.xin.
+// PIPE = true: A.nst stages in one cooperative launch; each CTA walks the
+// same tiles in every stage, so a tile's state (c, acc) is only ever touched
+// by one CTA, in stage order, and the only exchange between CTAs is the
+// state planes, guarded by the per-(block, column tile) counters.
+template <bool RK4, bool PIPE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUtensorMap tmUl,
-          const __grid_constant__ CUtensorMap tmTh, const __grid_constant__ CUtensorMap tmTl,
-          const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl, TcArgs A)
+tc_kernel(const __grid_constant__ TcMaps M, const TcArgs A)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -297,15 +319,29 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
         // ------------------------------------------------------- TMA producer
         if (lane == 0) {
             int it = 0;
+            for (int g = 0; g < (PIPE ? A.nst : 1) && !*abort; ++g) {
+            const int buf = PIPE ? (int)((A.t0 + g) % TC_NBUF) : A.xin;
+            const CUtensorMap *tmXh = &M.Xh[buf], *tmXl = &M.Xl[buf];
             for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
                 const int l = t / (mt * nt), rem = t % (mt * nt);
                 const int i0 = (rem / nt) * TBM, c0 = (rem % nt) * TBN;
                 for (int part = 0; part < 2 && !*abort; ++part) {
                     if ((part == 0 && l >= A.lmax) || (part == 1 && l < 1)) continue;
-                    const CUtensorMap *ta_h = part == 0 ? &tmUh : &tmTh;
-                    const CUtensorMap *ta_l = part == 0 ? &tmUl : &tmTl;
+                    const CUtensorMap *ta_h = part == 0 ? &M.Uh : &M.Th;
+                    const CUtensorMap *ta_l = part == 0 ? &M.Ul : &M.Tl;
                     const int ablk = part == 0 ? l : l - 1;
-                    const int xcol = (part == 0 ? l + 1 : l - 1) * A.nb;
+                    const int xblk = part == 0 ? l + 1 : l - 1;
+                    const int xcol = xblk * A.nb;
+                    if (PIPE && g > 0) {
+                        // block xblk's planes of this stage: written by the
+                        // previous stage's epilogues of its mt row tiles
+                        if (!wait_count(A.cnt + xblk * nt + rem % nt, g * mt * EPI_WARPS, abort, A.err)) {
+                            *abort = 1;
+                            atomicOr(A.err, kErrTimeout);
+                            break;
+                        }
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
+                    }
                     for (int kt = 0; kt < nk; ++kt, ++it) {
                         const int s = it % TST;
                         if (it >= TST &&
@@ -315,11 +351,12 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
                         mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                         tma_load_3d(st, ta_h, kt * TBK, i0, ablk, &full[s]);
                         tma_load_3d(st + A_BYTES, ta_l, kt * TBK, i0, ablk, &full[s]);
-                        tma_load_2d(st + 2 * A_BYTES, &tmXh, xcol + kt * TBK, c0, &full[s]);
-                        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tmXl, xcol + kt * TBK, c0, &full[s]);
+                        tma_load_2d(st + 2 * A_BYTES, tmXh, xcol + kt * TBK, c0, &full[s]);
+                        tma_load_2d(st + 2 * A_BYTES + B_BYTES, tmXl, xcol + kt * TBK, c0, &full[s]);
                         issued = it + 1;
                     }
                 }
+            }
             }
         }
     } else if (warp == 1) {
@@ -327,6 +364,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16(TBM, TBN);
             int it = 0, j = 0;
+            for (int g = 0; g < (PIPE ? A.nst : 1) && !*abort; ++g)
             for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++j) {
                 const int l = t / (mt * nt);
                 const int T = nk * ((l < A.lmax ? 1 : 0) + (l >= 1 ? 1 : 0));
@@ -360,6 +398,23 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
         const int quarter = warp & 3;                    // TMEM lanes this warp may read
         const int part = (warp - 2) >> 2;                // which EPI_CPW chunks of the TBN columns
         int j = 0;
+        bool stop = false;
+        for (int g = 0; g < (PIPE ? A.nst : 1) && !stop; ++g) {
+        // this stage's arguments (the launch's own for one stage)
+        TcArgs As = A;
+        if (PIPE) {
+            const long long tg = A.t0 + g;
+            const long long k = tg / A.per;
+            const int q = (int)(tg % A.per) + (RK4 ? 0 : 1);
+            const int h = RK4 ? (q == 0 ? 0 : (q == 3 ? 2 : 1)) : (A.hold ? 1 : 0);
+            As.k = k;
+            As.stage = q;
+            if (!RK4) As.term_dt = df_from_double(A.dt / (double)q);
+            As.fdf = A.fdf_all + ((size_t)k * 3 + h) * A.B;
+            const int ob = (int)((tg + 1) % TC_NBUF);
+            As.xo_h = A.xh[ob];
+            As.xo_l = A.xl[ob];
+        }
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
             const int l = t / (mt * nt), rem = t % (mt * nt);
             const int i0 = (rem / nt) * TBM, c0 = (rem % nt) * TBN;
@@ -367,14 +422,14 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
             const int ab = j & 1;
             bool have = mbar_wait_bounded(&acc_full[ab], (uint32_t)((j >> 1) & 1), abort, TC_WAIT_NS);
             have = __all_sync(0xffffffffu, have);
-            if (!have) break;
+            if (!have) { stop = true; break; }
             tc_fence_after();
             const int row = i0 + quarter * 32 + lane;
             const long long a = (long long)l * n + row;
             const long long col = (long long)l * A.nb + row;
             const bool valid_row = row < n;
             df e{0.f, 0.f};
-            if (valid_row) { const float2 ev = A.Edf[a]; e = df{ev.x, ev.y}; }
+            if (valid_row) { const float2 ev = As.Edf[a]; e = df{ev.x, ev.y}; }
 #pragma unroll 1
             for (int chunk = part * EPI_CPW; chunk < (part + 1) * EPI_CPW; ++chunk) {
                 float v[16];
@@ -385,31 +440,38 @@ tc_kernel(const __grid_constant__ CUtensorMap tmUh, const __grid_constant__ CUte
                     for (int q = 0; q < 16; ++q) v[q] = 0.f;
                 }
                 if (valid_row) {
-                    const bool from_c = RK4 ? (A.stage == 0) : (A.stage == 1);
+                    const bool from_c = RK4 ? (As.stage == 0) : (As.stage == 1);
 #pragma unroll
-                    for (int g = 0; g < 8; g += TC_LOAD_GROUP) {
+                    for (int gg = 0; gg < 8; gg += TC_LOAD_GROUP) {
                         TcIn<RK4> in[TC_LOAD_GROUP];
                         float2 fv[TC_LOAD_GROUP];
 #pragma unroll
                         for (int u = 0; u < TC_LOAD_GROUP; ++u) {
-                            const int b = c0 / 2 + chunk * 8 + g + u;      // pulse
-                            if (b < A.B) {
-                                tc_load<RK4>(A, (long long)b * A.N + a, from_c, in[u]);
-                                fv[u] = __ldg(A.fdf + b);
+                            const int b = c0 / 2 + chunk * 8 + gg + u;      // pulse
+                            if (b < As.B) {
+                                tc_load<RK4>(As, (long long)b * As.N + a, from_c, in[u]);
+                                fv[u] = __ldg(As.fdf + b);
                             }
                         }
 #pragma unroll
                         for (int u = 0; u < TC_LOAD_GROUP; ++u) {
-                            const int jj = g + u;
+                            const int jj = gg + u;
                             const int b = c0 / 2 + chunk * 8 + jj;
-                            if (b < A.B) tc_update<RK4>(A, b, a, col, e, df{fv[u].x, fv[u].y}, v[2 * jj], v[2 * jj + 1], in[u]);
+                            if (b < As.B) tc_update<RK4>(As, b, a, col, e, df{fv[u].x, fv[u].y}, v[2 * jj], v[2 * jj + 1], in[u]);
                         }
                     }
                 }
             }
             tc_fence_before();
+            if (PIPE) {
+                // this warp's share of the tile's planes is written: count it
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) atomicAdd(A.cnt + l * nt + rem % nt, 1);
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
+        }
         }
     }
     __syncthreads();
@@ -488,24 +550,72 @@ __global__ void tc_out_kernel(const float4 *__restrict__ cdf, double2 *__restric
     c[q] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
 }
 
+static int tc_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms < 1 ? 1 : sms;
+}
+
+static int tc_grid(int n, int lmax, int B)
+{
+    const int ntiles = ((n + TBM - 1) / TBM) * ((2 * B + TBN - 1) / TBN) * (lmax + 1);
+    const int sms = tc_sms();
+    return ntiles < sms ? ntiles : sms;
+}
+
 cudaError_t launch_tc(const TcMaps &m, const TcArgs &A, cudaStream_t stream)
 {
     const bool rk4 = A.mode == EPI_RK4;
-    const void *fn = rk4 ? (const void *)tc_kernel<true> : (const void *)tc_kernel<false>;
+    const void *fn = rk4 ? (const void *)tc_kernel<true, false> : (const void *)tc_kernel<false, false>;
     const cudaError_t ea = ensure_dyn_smem(fn, TC_SMEM);
     if (ea != cudaSuccess) return ea;
-    int sms = 0;
-    {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-    }
-    const int ntiles = ((A.n + TBM - 1) / TBM) * ((2 * A.B + TBN - 1) / TBN) * (A.lmax + 1);
-    const int grid = ntiles < sms ? ntiles : sms;
-    if (rk4) tc_kernel<true><<<grid, TC_THREADS, TC_SMEM, stream>>>(m.Uh, m.Ul, m.Th, m.Tl, m.Xh, m.Xl, A);
-    else tc_kernel<false><<<grid, TC_THREADS, TC_SMEM, stream>>>(m.Uh, m.Ul, m.Th, m.Tl, m.Xh, m.Xl, A);
+    const int grid = tc_grid(A.n, A.lmax, A.B);
+    if (rk4) tc_kernel<true, false><<<grid, TC_THREADS, TC_SMEM, stream>>>(m, A);
+    else tc_kernel<false, false><<<grid, TC_THREADS, TC_SMEM, stream>>>(m, A);
     return cudaGetLastError();
+}
+
+int tc_pipe_counters(int lmax, int B) { return (lmax + 1) * ((2 * B + TBN - 1) / TBN); }
+
+bool tc_pipe_fits(int n, int lmax, int B)
+{
+    for (int rk4 = 0; rk4 < 2; ++rk4) {
+        const void *fn = rk4 ? (const void *)tc_kernel<true, true> : (const void *)tc_kernel<false, true>;
+        if (ensure_dyn_smem(fn, TC_SMEM) != cudaSuccess) return false;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TC_THREADS, TC_SMEM) != cudaSuccess || nb < 1)
+            return false;
+        if ((long long)nb * tc_sms() < tc_grid(n, lmax, B)) return false;
+    }
+    return true;
+}
+
+cudaError_t launch_tc_pipe(const TcMaps &m, const TcArgs &A, cudaStream_t stream)
+{
+    const bool rk4 = A.mode == EPI_RK4;
+    const void *fn = rk4 ? (const void *)tc_kernel<true, true> : (const void *)tc_kernel<false, true>;
+    const cudaError_t ea = ensure_dyn_smem(fn, TC_SMEM);
+    if (ea != cudaSuccess) return ea;
+    // zero the counters, then one cooperative launch: CTAs wait for one
+    // another's tiles, so all of them must be resident together
+    const cudaError_t z = cudaMemsetAsync(A.cnt, 0, sizeof(int) * (size_t)tc_pipe_counters(A.lmax, A.B), stream);
+    if (z != cudaSuccess) return z;
+    TcMaps mm = m;
+    TcArgs aa = A;
+    void *args[] = {(void *)&mm, (void *)&aa};
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(tc_grid(A.n, A.lmax, A.B));
+    lc.blockDim = dim3(TC_THREADS);
+    lc.dynamicSmemBytes = TC_SMEM;
+    lc.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelExC(&lc, fn, args);
 }
 
 cudaError_t launch_tc_in(const double2 *c, float4 *cdf, __nv_bfloat16 *xh, __nv_bfloat16 *xl, long long N, int n,

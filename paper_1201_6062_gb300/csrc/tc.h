@@ -7,10 +7,16 @@
 
 namespace tdse {
 
+// Buffers of state planes: the per-stage launches alternate two; a
+// persistent launch rotates through four (a stage's planes are overwritten
+// three stages later, by when every tile that read them has finished).
+constexpr int TC_NBUF = 4;
+
 // TMA descriptors: dipole planes (hi, lo), transposed dipole planes (hi, lo)
-// and the current input state planes (hi, lo).
+// and the state planes (hi, lo) of every buffer.
 struct TcMaps {
-    CUtensorMap Uh, Ul, Th, Tl, Xh, Xl;
+    CUtensorMap Uh, Ul, Th, Tl;
+    CUtensorMap Xh[TC_NBUF], Xl[TC_NBUF];
 };
 
 // Output tile columns (pulse planes) per CTA tile; also the row count of the
@@ -33,9 +39,26 @@ struct TcArgs {
                             // previous stage), x unused; Taylor: x previous term, acc partial sum (float-float)
     __nv_bfloat16 *xo_h, *xo_l;   // output planes [2B][plane]
     int *err;
+    int xin;                // per-stage launch: the buffer holding the stage's input planes
+    // Persistent launch of nst stages (launch_tc_pipe): stage g of the launch
+    // is stage t0 + g of the propagation (per stages per step); it reads
+    // buffer (t0 + g) % TC_NBUF and writes the next.  A tile of stage g waits
+    // until every epilogue warp of the previous stage's tiles in the two
+    // blocks it reads (for its pulse columns) has counted itself in cnt.
+    int nst, per;
+    long long t0;
+    double dt;
+    const float2 *fdf_all;  // field values [(k*3 + h)*B + b]
+    __nv_bfloat16 *xh[TC_NBUF], *xl[TC_NBUF];
+    int *cnt;               // [(lmax+1) * column tiles], zero at launch
 };
 
 cudaError_t launch_tc(const TcMaps &m, const TcArgs &A, cudaStream_t stream);
+// Whether the persistent launch can have all its CTAs resident (one per SM).
+bool tc_pipe_fits(int n, int lmax, int B);
+cudaError_t launch_tc_pipe(const TcMaps &m, const TcArgs &A, cudaStream_t stream);
+// Counters the persistent launch needs: (lmax+1) * column tiles.
+int tc_pipe_counters(int lmax, int B);
 cudaError_t launch_tc_in(const double2 *c, float4 *cdf, __nv_bfloat16 *xh, __nv_bfloat16 *xl, long long N, int n,
                          int nb, long long plane, int B, cudaStream_t stream);
 cudaError_t launch_tc_field(const double *field, int S, int sps, long long nsteps, int B, float2 *fdf,

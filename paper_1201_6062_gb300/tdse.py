@@ -59,6 +59,7 @@ _SIGS = {
     "tdse_inject_wait_timeout": ([_vp, _l, _vp], _i),
     "tdse_group_plan_info": ([_vp, _i] + [ctypes.POINTER(_i)] * 7, _i),
     "tdse_group_set_persistent": ([_vp, _i, _i, _i], _i),
+    "tdse_set_batch_persistent": ([_vp, _i], _i),
     "tdse_group_persistent_info": ([_vp] + [ctypes.POINTER(_i)] * 5, _i),
 }
 class _FieldFn(ctypes.Structure):
@@ -269,6 +270,10 @@ class Hamiltonian:
     def inject_wait_timeout(self, timeout_ns, stream=None):
         """Test hook: one bounded device wait runs out after timeout_ns; the next sync() raises ETIMEOUT."""
         _check(_lib.tdse_inject_wait_timeout(self._h, int(timeout_ns), _stream(stream)))
+
+    def set_batch_persistent(self, on=True):
+        """bf16x3: run every stage of a batch in one persistent launch (default) or one launch per stage."""
+        _check(_lib.tdse_set_batch_persistent(self._h, 1 if on else 0))
 
     def plan_info(self):
         """Launch shape of the block product: dict(ctas, ctas_per_sm, threads, ring, persistent)."""

@@ -182,3 +182,42 @@ def test_bf16x3_context_rejects_single_system_calls(tdse_lib):
     # populations still work on such a context
     p = H.populations(c)
     assert abs(p["bound"].item() - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("lmax,n,B,nsteps,scheme", [(3, 300, 9, 7, "rk4"), (4, 300, 256, 3, "rk4"), (0, 40, 3, 5, "rk4"),
+                                                    (15, 1000, 256, 2, "rk4"), (3, 300, 9, 5, "taylor")])
+def test_bf16x3_persistent_launch_equals_launch_per_stage(tdse_lib, lmax, n, B, nsteps, scheme):
+    """Every stage in one persistent launch (tiles of the next stage start as
+    soon as the tiles they read are done) gives the same bits as one launch
+    per stage: the same products and updates, only scheduled differently.
+    (15, 1000, 256): the sweep shape, 512 tiles on the SMs."""
+    dt, sps = 0.02, 1
+    E, U, F, C0 = sweep(lmax, n, B, nsteps, sps)
+    H = tdse_lib.Hamiltonian(E, U, lmax, n, "bf16x3")
+    f = torch.from_numpy(F.reshape(-1)).cuda()
+    out = {}
+    for on in (True, False):
+        H.set_batch_persistent(on)
+        c = torch.from_numpy(C0.reshape(-1).copy()).cuda()
+        H.propagate_batch(c, f, B, dt, nsteps, scheme, order=6)
+        H.sync()
+        out[on] = c.cpu().numpy()
+    assert np.array_equal(out[True], out[False])
+    b = B - 1
+    if scheme == "rk4":
+        ref, _ = oracle.rk4(lmax, n, E, U, C0[b], F[b], dt, nsteps)
+    else:
+        ref, _ = oracle.taylor(lmax, n, E, U, C0[b], F[b], dt, nsteps, 6)
+    assert rel(out[True].reshape(B, -1)[b], ref) < 1e-5
+
+
+def test_batch_persistent_switch_errors(tdse_lib):
+    E = inputs.energies(1, 64)
+    H = tdse_lib.Hamiltonian(E, inputs.dipoles(1, 64, 1), 1, 64, "df32")
+    with pytest.raises(tdse_lib.TDSEError) as ex:
+        H.set_batch_persistent(True)
+    assert ex.value.status == tdse_lib.ENOTSUP
+    H2 = tdse_lib.Hamiltonian(E, inputs.dipoles(1, 64, 1), 1, 64, "bf16x3")
+    with pytest.raises(tdse_lib.TDSEError) as ex:
+        tdse_lib._check(tdse_lib._lib.tdse_set_batch_persistent(H2.handle, 2))
+    assert ex.value.status == tdse_lib.EINVAL
