@@ -501,12 +501,14 @@ tdse_status tdse_group_tuning_load(tdse_group *g, const char *path, int *applied
 /*
  * tdse_set_batch_persistent — bf16x3 contexts: on = 1 (the default) runs
  * every stage of a tdse_propagate_batch call in one cooperative launch (per
- * 2^20 stages), each CTA walking its output tiles stage after stage; a tile
- * of the next stage starts once every tile of the previous stage in the two
- * blocks it reads (for its pulse columns) has written its state planes
- * (per-(block, column tile) counters with bounded waits; the planes rotate
- * through four buffers).  on = 0: one launch per stage.  Both give the same
- * results bit for bit.  Errors: EINVAL, ENOTSUP (not a bf16x3 context).
+ * 2^20 stages), the output tiles of all stages dealt round-robin over the
+ * CTAs; a tile of the next stage loads the state planes of blocks l-1 and
+ * l+1 once every tile of those blocks (for its pulse columns) has written
+ * them in the previous stage, and updates its own state once block l's
+ * tiles have (per-(block, column tile) counters with bounded waits; the
+ * planes rotate through four buffers).  on = 0: one launch per stage.  Both
+ * give the same results bit for bit.  Errors: EINVAL, ENOTSUP (not a bf16x3
+ * context).
  */
 tdse_status tdse_set_batch_persistent(tdse_ctx *ctx, int on);
 

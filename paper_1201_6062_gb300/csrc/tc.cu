@@ -263,10 +263,13 @@ __device__ __forceinline__ bool wait_count(const int *c, int need, volatile int 
 }
 
 // PIPE = false: one stage per launch, input planes in buffer A.xin.
-// PIPE = true: A.nst stages in one cooperative launch; each CTA walks the
-// same tiles in every stage, so a tile's state (c, acc) is only ever touched
-// by one CTA, in stage order, and the only exchange between CTAs is the
-// state planes, guarded by the per-(block, column tile) counters.
+// PIPE = true: A.nst stages in one cooperative launch.  The tiles of all
+// stages form one list dealt round-robin over the CTAs, so a tile may be
+// updated by another CTA than in the previous stage.  Every epilogue warp
+// counts itself per (block, column tile) once it has written its share of
+// the tile's state and planes; a tile's loads of the planes of blocks l-1
+// and l+1 wait for those blocks' counts of the previous stage, and its
+// update of its own state waits for block l's.
 template <bool RK4, bool PIPE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 tc_kernel(const __grid_constant__ TcMaps M, const TcArgs A)
@@ -288,6 +291,10 @@ tc_kernel(const __grid_constant__ TcMaps M, const TcArgs A)
     const int mt = (n + TBM - 1) / TBM;
     const int nt = (2 * A.B + TBN - 1) / TBN;
     const int ntiles = mt * nt * (A.lmax + 1);
+    // Work items: tile t of stage g is item g * ntiles + t, dealt round-robin
+    // over the CTAs (in a persistent launch the load of the CTAs that take an
+    // extra tile rotates from stage to stage).
+    const long long nitems = (long long)(PIPE ? A.nst : 1) * ntiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TST; ++s) {
@@ -319,10 +326,10 @@ tc_kernel(const __grid_constant__ TcMaps M, const TcArgs A)
         // ------------------------------------------------------- TMA producer
         if (lane == 0) {
             int it = 0;
-            for (int g = 0; g < (PIPE ? A.nst : 1) && !*abort; ++g) {
-            const int buf = PIPE ? (int)((A.t0 + g) % TC_NBUF) : A.xin;
-            const CUtensorMap *tmXh = &M.Xh[buf], *tmXl = &M.Xl[buf];
-            for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+            for (long long w = blockIdx.x; w < nitems && !*abort; w += gridDim.x) {
+                const int g = (int)(w / ntiles), t = (int)(w % ntiles);
+                const int buf = PIPE ? (int)((A.t0 + g) % TC_NBUF) : A.xin;
+                const CUtensorMap *tmXh = &M.Xh[buf], *tmXl = &M.Xl[buf];
                 const int l = t / (mt * nt), rem = t % (mt * nt);
                 const int i0 = (rem / nt) * TBM, c0 = (rem % nt) * TBN;
                 for (int part = 0; part < 2 && !*abort; ++part) {
@@ -357,16 +364,14 @@ tc_kernel(const __grid_constant__ TcMaps M, const TcArgs A)
                     }
                 }
             }
-            }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16(TBM, TBN);
             int it = 0, j = 0;
-            for (int g = 0; g < (PIPE ? A.nst : 1) && !*abort; ++g)
-            for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++j) {
-                const int l = t / (mt * nt);
+            for (long long w = blockIdx.x; w < nitems && !*abort; w += gridDim.x, ++j) {
+                const int l = (int)(w % ntiles) / (mt * nt);
                 const int T = nk * ((l < A.lmax ? 1 : 0) + (l >= 1 ? 1 : 0));
                 const int ab = j & 1;
                 if (j >= 2 && !mbar_wait_bounded(&acc_empty[ab], (uint32_t)(((j >> 1) - 1) & 1), abort, TC_WAIT_NS))
@@ -397,12 +402,12 @@ tc_kernel(const __grid_constant__ TcMaps M, const TcArgs A)
         // ------------------------------------------ epilogue: warps 2..17
         const int quarter = warp & 3;                    // TMEM lanes this warp may read
         const int part = (warp - 2) >> 2;                // which EPI_CPW chunks of the TBN columns
-        int j = 0;
-        bool stop = false;
-        for (int g = 0; g < (PIPE ? A.nst : 1) && !stop; ++g) {
-        // this stage's arguments (the launch's own for one stage)
-        TcArgs As = A;
-        if (PIPE) {
+        int j = 0, cur = -1;
+        TcArgs As = A;                  // the item's stage arguments (the launch's own for one stage)
+        for (long long w = blockIdx.x; w < nitems; w += gridDim.x, ++j) {
+        const int g = (int)(w / ntiles), t = (int)(w % ntiles);
+        if (PIPE && g != cur) {
+            cur = g;
             const long long tg = A.t0 + g;
             const long long k = tg / A.per;
             const int q = (int)(tg % A.per) + (RK4 ? 0 : 1);
@@ -415,14 +420,24 @@ tc_kernel(const __grid_constant__ TcMaps M, const TcArgs A)
             As.xo_h = A.xh[ob];
             As.xo_l = A.xl[ob];
         }
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+        {
             const int l = t / (mt * nt), rem = t % (mt * nt);
             const int i0 = (rem / nt) * TBM, c0 = (rem % nt) * TBN;
             const int T = nk * ((l < A.lmax ? 1 : 0) + (l >= 1 ? 1 : 0));
             const int ab = j & 1;
             bool have = mbar_wait_bounded(&acc_full[ab], (uint32_t)((j >> 1) & 1), abort, TC_WAIT_NS);
             have = __all_sync(0xffffffffu, have);
-            if (!have) { stop = true; break; }
+            if (!have) break;
+            if (PIPE && g > 0) {
+                // the tile's state (c, acc): written in the previous stage,
+                // possibly by another CTA; every thread acquires the count
+                const bool ok = __all_sync(0xffffffffu, wait_count(A.cnt + l * nt + rem % nt, g * mt * EPI_WARPS,
+                                                                   abort, A.err));
+                if (!ok) {
+                    if (lane == 0) { *abort = 1; atomicOr(A.err, kErrTimeout); }
+                    break;
+                }
+            }
             tc_fence_after();
             const int row = i0 + quarter * 32 + lane;
             const long long a = (long long)l * n + row;
