@@ -506,7 +506,7 @@ tdse_status tdse_group_tuning_load(tdse_group *g, const char *path, int *applied
  * l+1 once every tile of those blocks (for its pulse columns) has written
  * them in the previous stage, and updates its own state once block l's
  * tiles have (per-(block, column tile) counters with bounded waits; the
- * planes rotate through four buffers).  on = 0: one launch per stage.  Both
+ * planes alternate between two buffers).  on = 0: one launch per stage.  Both
  * give the same results bit for bit.  Errors: EINVAL, ENOTSUP (not a bf16x3
  * context).
  */

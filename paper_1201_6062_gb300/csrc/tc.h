@@ -7,10 +7,11 @@
 
 namespace tdse {
 
-// Buffers of state planes: the per-stage launches alternate two; a
-// persistent launch rotates through four (a stage's planes are overwritten
-// three stages later, by when every tile that read them has finished).
-constexpr int TC_NBUF = 4;
+// Buffers of state planes, alternated by stage.  Two suffice in the
+// persistent launch too: a tile writing block l's planes for the next stage
+// has waited for the previous stage's tiles of blocks l-1 and l+1, which are
+// the only tiles that read block l's planes from that buffer.
+constexpr int TC_NBUF = 2;
 
 // TMA descriptors: dipole planes (hi, lo), transposed dipole planes (hi, lo)
 // and the state planes (hi, lo) of every buffer.
