@@ -13,7 +13,10 @@
 // its state loads, so it gets as many warps as the register file allows).  The batched state is float-float
 // (FP32 hi + lo, about 44 bits): the GB300 FP64 pipe is 1/64 of the FP32
 // pipe, and an FP64 state update would cost more than the products.
-// All waits are bounded (sync.cuh).
+// A propagation runs either one launch per stage or (the default) one
+// persistent cooperative launch for all its stages, whose tiles of the next
+// stage start as soon as the tiles they read have finished (tc_kernel's
+// PIPE mode).  All waits are bounded (sync.cuh).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
