@@ -53,10 +53,12 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
 __device__ __forceinline__ bool grid_sync(unsigned *ctr, unsigned target, volatile int *abort, int *err,
                                           volatile int *go, int tid, int nthreads)
 {
-    __threadfence();
+    // the CTA barrier orders every thread's writes before thread 0's fence,
+    // which makes them visible at GPU scope before its arrival
     named_sync(1, nthreads);
     if (tid == 0) {
         int ok = !*abort;
+        __threadfence();
         if (ok) {
             atomicAdd(ctr, 1u);
             volatile int *gerr = err;
